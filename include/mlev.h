@@ -1,0 +1,201 @@
+/*
+ * mlev - multilevel local and parallel P1 finite element eigensolver on one GPU.
+ *
+ * Computes the smallest eigenpair (lambda_{h_n}, u_{h_n}) of
+ *     a(u, v) = lambda b(u, v)  for all v in V_{0h}(Omega),   b(u, u) = 1,
+ * with a(u, v) = (kappa grad u, grad v) and b(u, v) = (u, v) (paper Section 3,
+ * Eq. Weak_Eigenvalue_Problem), by Algorithm 4.2 of Li, Han, Xie, You ("Local and
+ * parallel finite element algorithm based on multilevel discretization for
+ * eigenvalue problem"): an eigenproblem on V_{0h_1}, then n-1 applications of the
+ * one correction step of Algorithm 4.1 (local auxiliary problems on Omega_j,
+ * gluing with the G_{m+1} boundary value problem, Rayleigh-Ritz on
+ * V_{0H} + span{u~}).
+ *
+ * Geometry: T_H is a grid of ncx x ncy square cells of side H (origin x0, y0), a
+ * cell mask selects Omega, and every cell is split by its SW-NE diagonal. Level k
+ * has mesh size h_k = H / 2^k (T_{h_1} is one regular refinement of T_H,
+ * Section 4.2). All nodal arrays are row-major with x fastest; a level-k lattice
+ * has (ncy*2^k + 1) rows of (ncx*2^k + 1) nodes.
+ *
+ * Conventions for every call:
+ *  - Return value: MLEV_OK (0) or a negative MLEV_E* code; mlev_last_error()
+ *    gives a message. No C++ exception crosses this interface.
+ *  - Host arrays passed to mlev_set_* are copied before the call returns.
+ *  - Device buffers (workspace, kappa when kappa_on_device, outputs) are owned by
+ *    the caller. The library never allocates device memory; mlev_solve works only
+ *    inside the caller's workspace and launches on the caller's stream.
+ *  - One context must not be used from two host threads at once.
+ */
+#ifndef MLEV_H
+#define MLEV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLEV_OK 0
+#define MLEV_EINVAL (-1)        /* bad argument or inconsistent setup */
+#define MLEV_ENOMEM (-2)        /* workspace too small / host allocation failed */
+#define MLEV_ECUDA (-3)         /* a CUDA runtime call failed */
+#define MLEV_ENOCONV (-4)       /* an iteration hit its cap before its tolerance */
+#define MLEV_ETIMEOUT (-5)      /* a bounded device-side wait gave up */
+#define MLEV_EUNSUPPORTED (-6)  /* valid input outside what this build implements */
+#define MLEV_ESTATE (-7)        /* call order violated (e.g. solve before setup) */
+
+#define MLEV_KAPPA_ONE 0             /* kappa == 1 (the Laplacian of Example 1) */
+#define MLEV_KAPPA_PER_COARSE_CELL 1 /* kappa[b][cj][ci], constant on each cell of T_H */
+#define MLEV_KAPPA_PER_FINE_ELEM 2   /* kappa[b][cj][ci][t] on triangles of T_{h_n}; t=0 lower, t=1 upper */
+
+#define MLEV_GLUE_PAPER 0  /* Algorithm 4.1 step 2: u~ = u~^j on closed G_j, G_{m+1} problem elsewhere */
+
+#define MLEV_PREC_FP64 0   /* every kernel in FP64 (the plain method) */
+#define MLEV_PREC_MIXED 1  /* FP32 multigrid for local/strip solves + FP64 residual refinement */
+
+#define MLEV_MAX_LEVELS 10
+
+typedef struct mlev_ctx mlev_ctx;
+
+/* Solver options. Fill with mlev_opts_default() and override fields. */
+typedef struct mlev_opts {
+  int precision;        /* MLEV_PREC_MIXED or MLEV_PREC_FP64 */
+  int vcycles;          /* V-cycles per solve pass of each auxiliary problem (Eq. Aux_Problem) */
+  int refine_passes;    /* solve passes; passes after the first start from an FP64 residual */
+  int strip_vcycles;    /* V-cycles per pass for the G_{m+1} problem (Eq. G_m+1_Problem) */
+  int pre_smooth;       /* red-black Gauss-Seidel sweeps before restriction */
+  int post_smooth;      /* sweeps after prolongation */
+  int coarse_sweeps;    /* sweeps on the coarsest grid of each multigrid hierarchy */
+  int level1_max_iter;  /* iteration cap of the level-1 eigensolver (Algorithm 4.2 step 1) */
+  double level1_tol;    /* relative eigen-residual target of the level-1 eigensolver */
+  int rr_max_iter;      /* Newton/bisection cap of the Rayleigh-Ritz step */
+  int use_graph;        /* 1: capture the launch sequence in a CUDA graph and replay it */
+  double omega;         /* over-relaxation of the red-black Gauss-Seidel smoother (1 = plain GS) */
+  int check_residuals;  /* 1: measure the final relative residual of every local / G_{m+1} solve */
+  int profile;          /* 1: time every launch with CUDA events (no graph); read with mlev_profile_read */
+  int reserved[4];
+} mlev_opts;
+
+/* Per-solve diagnostics (batch member 0 unless noted). */
+typedef struct mlev_report {
+  int levels;                          /* n */
+  int batch;                           /* B */
+  double lambda[MLEV_MAX_LEVELS + 1];  /* lambda_{h_k} for k = 1..n (index k) */
+  int level1_iters;                    /* max over the batch */
+  double level1_residual;              /* max over the batch */
+  int rr_iters[MLEV_MAX_LEVELS + 1];   /* max over the batch */
+  double local_residual[MLEV_MAX_LEVELS + 1];  /* max over jobs of ||f - A e|| / ||f|| (check_residuals) */
+  double strip_residual[MLEV_MAX_LEVELS + 1];  /* same for the G_{m+1} problem (check_residuals) */
+  long long n_fine;                    /* interior nodes of T_{h_n} (unknowns per problem) */
+  long long n_local_fine;              /* sum over j of unknowns of Omega_j on T_{h_n} */
+  long long n_strip_fine;              /* unknowns of the G_{m+1} problem on T_{h_n} */
+  int n_coarse;                        /* interior nodes of T_H */
+  int kernel_launches;                 /* launches issued by the last mlev_solve (graph nodes if replayed) */
+  int status_flags;                    /* device-side status bits (0 = clean) */
+  long long h2d_bytes;                 /* host-to-device bytes copied by this call */
+  long long d2h_bytes;                 /* device-to-host bytes copied by this call (outputs only) */
+} mlev_report;
+
+/* Per-kernel-family timing of the last solve run with opts.profile = 1. */
+typedef struct mlev_kernel_stat {
+  char name[32];   /* kernel family, e.g. "mg_smooth" */
+  int launches;    /* launches in that solve */
+  double ms;       /* summed CUDA-event durations of those launches (events on the solve's stream) */
+  double bytes;    /* algorithmic bytes those launches must move (the library's traffic model) */
+} mlev_kernel_stat;
+
+/* Fill opts with the defaults of this build. */
+void mlev_opts_default(mlev_opts* opts);
+
+/* Create a context bound to CUDA device `device`. *out is NULL on failure.
+ * device == -1 creates a planning-only context: every mlev_set_*, mlev_workspace_size
+ * and mlev_problem_info works (no GPU needed); mlev_solve* return MLEV_ESTATE. */
+int mlev_create(mlev_ctx** out, int device);
+
+/* Destroy a context (NULL is ignored). Does not touch caller-owned device memory. */
+void mlev_destroy(mlev_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none); valid until the next call. */
+const char* mlev_last_error(const mlev_ctx* ctx);
+
+/*
+ * Coarse triangulation T_H (Section 2.1; Section 4 "coarsest triangulation"):
+ * ncx x ncy cells of side H from (x0, y0); cell_in[cj*ncx + ci] != 0 marks cells of
+ * Omega. Each cell is split by its SW-NE diagonal. Requires 2 <= ncx, ncy <= 64.
+ */
+int mlev_set_domain(mlev_ctx* ctx, int ncx, int ncy, double x0, double y0, double H,
+                    const uint8_t* cell_in);
+
+/*
+ * Domain decomposition (Section 4, before Algorithm 4.1): cell_owner[cj*ncx+ci] = j
+ * in [0, m) for the disjoint D_j (-1 on cells outside Omega); overlap[j] = number
+ * of coarse cells by which D_j is enlarged (Chebyshev distance) to Omega_j; delta =
+ * inset defining the closed G_j = { x in closure(D_j) : dist_inf(x, dD_j \ dOmega) >= delta },
+ * a positive multiple of H/4. Every D_j must be a rectangle of cells (else
+ * MLEV_EUNSUPPORTED); the closed G_j must be pairwise disjoint (else MLEV_EINVAL).
+ * glue_mode must be MLEV_GLUE_PAPER.
+ */
+int mlev_set_partition(mlev_ctx* ctx, int m, const int32_t* cell_owner, const int32_t* overlap,
+                       double delta, int glue_mode);
+
+/* Number of levels n >= 2 (h_k = H / 2^k, k = 1..n; Section 4.2, Algorithm 4.2). */
+int mlev_set_levels(mlev_ctx* ctx, int n);
+
+/*
+ * Bilinear forms (Section 2.2, Section 3): a(u,v) = (kappa grad u, grad v),
+ * b(u,v) = (u,v), for `batch` independent problems sharing the geometry.
+ * kappa layout by kind: ONE -> kappa ignored (may be NULL); PER_COARSE_CELL ->
+ * [batch][ncy][ncx]; PER_FINE_ELEM -> [batch][ncy*2^n][ncx*2^n][2]. Values must be
+ * positive on cells of Omega. If kappa_on_device != 0 the pointer is a device
+ * buffer the caller keeps alive and unchanged-in-layout while solving (it is read
+ * at every mlev_solve); otherwise it is copied now (call mlev_set_levels first
+ * for PER_FINE_ELEM).
+ */
+int mlev_set_forms(mlev_ctx* ctx, int batch, int kappa_kind, const double* kappa, int kappa_on_device);
+
+/* Bytes of device workspace mlev_solve needs for the current setup and opts. */
+int mlev_workspace_size(mlev_ctx* ctx, const mlev_opts* opts, size_t* bytes);
+
+/* Unknown counts of the current setup (any pointer may be NULL). */
+int mlev_problem_info(mlev_ctx* ctx, long long* n_fine, long long* n_local_fine, long long* n_strip_fine,
+                      int* n_coarse);
+
+/*
+ * Run Algorithm 4.2 for every batch member on `stream` (a cudaStream_t; NULL =
+ * legacy default stream).
+ *  workspace  : device buffer of >= mlev_workspace_size() bytes, 256-byte aligned,
+ *               owned by the caller. The first solve with a given workspace
+ *               uploads the plan tables into it (issue that first call before
+ *               any stream capture).
+ *  lambda_out : device array [batch] receiving lambda_{h_n}.
+ *  u_out      : NULL or device array [batch][(ncy*2^n+1)*(ncx*2^n+1)] receiving
+ *               u_{h_n} with b(u,u) = 1 and int u > 0, zero on and outside dOmega.
+ *  rep        : NULL or host report; non-NULL makes the call synchronize `stream`.
+ * Asynchronous when rep == NULL: errors found on the device then surface in the
+ * next call that synchronizes (a non-NULL rep).
+ */
+int mlev_solve(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
+               double* lambda_out, double* u_out, mlev_report* rep);
+
+/*
+ * Same as mlev_solve with HOST buffers: copies kappa_host (layout of
+ * mlev_set_forms, may be NULL to keep the current coefficients) to the device,
+ * solves, and copies lambda (and u if u_host != NULL) back, synchronizing stream.
+ * The kappa staging area is part of the workspace (mlev_workspace_size counts it).
+ */
+int mlev_solve_host(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
+                    const double* kappa_host, double* lambda_host, double* u_host, mlev_report* rep);
+
+/*
+ * Copy the per-family statistics of the last profiled solve (opts.profile = 1) into
+ * out[0 .. min(capacity, families) - 1]; *count receives the number of families.
+ * Returns MLEV_ESTATE if no profiled solve has completed on ctx.
+ */
+int mlev_profile_read(mlev_ctx* ctx, mlev_kernel_stat* out, int capacity, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLEV_H */

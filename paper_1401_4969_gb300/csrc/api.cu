@@ -1,0 +1,725 @@
+// C ABI of the mlev library and the launch sequence of Algorithm 4.2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kern_launch.h"
+#include "plan.h"
+
+using namespace mlev;
+
+struct ProfRecHost {
+  int launches = 0;
+  double ms = 0.0, bytes = 0.0;
+};
+
+struct mlev_ctx {
+  int device = 0;
+  Plan plan;
+  std::string err;
+  // plan tables are (re)uploaded when the workspace, the plan or the options change
+  const void* uploaded_ws = nullptr;
+  long long uploaded_version = -1;
+  long long version = 0;
+  bool kappa_dirty = true;
+  // captured graph
+  cudaGraphExec_t gexec = nullptr;
+  std::string graph_key;
+  int launches = 0;
+  int graph_launches = 0;
+  // plan cache: the planner runs again only when the setup or the precision changes
+  long long built_version = -1;
+  int built_precision = -1;
+  // profiling
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfRecHost> prof;
+  bool prof_valid = false;
+  long long io_h2d = 0, io_d2h = 0;  // bytes copied by the current call
+};
+
+namespace {
+
+int fail(mlev_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(mlev_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, MLEV_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t _e = (call);                          \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+  } while (0)
+
+int map_plan_error(mlev_ctx* ctx, const std::string& e) {
+  if (e.empty()) return MLEV_OK;
+  if (e.rfind("UNSUPPORTED", 0) == 0) return fail(ctx, MLEV_EUNSUPPORTED, e);
+  if (e.rfind("STATE", 0) == 0) return fail(ctx, MLEV_ESTATE, e);
+  return fail(ctx, MLEV_EINVAL, e);
+}
+
+bool opts_valid(const mlev_opts* o) {
+  return o && (o->precision == MLEV_PREC_FP64 || o->precision == MLEV_PREC_MIXED) && o->vcycles >= 1 &&
+         o->refine_passes >= 1 && o->strip_vcycles >= 1 && o->pre_smooth >= 0 && o->post_smooth >= 0 &&
+         o->pre_smooth + o->post_smooth >= 1 && o->coarse_sweeps >= 1 && o->level1_max_iter >= 1 &&
+         o->level1_tol > 0 && o->rr_max_iter >= 1 && o->omega > 0 && o->omega < 2;
+}
+
+std::string opts_key(const mlev_opts* o) {
+  char b[256];
+  snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%.17g/%d/%.17g/%d", o->precision, o->vcycles, o->refine_passes,
+           o->strip_vcycles, o->pre_smooth, o->post_smooth, o->coarse_sweeps, o->level1_max_iter, o->level1_tol,
+           o->rr_max_iter, o->omega, o->check_residuals);
+  return b;
+}
+
+template <typename P>
+P* at(void* base, const Span& s) {
+  return reinterpret_cast<P*>(static_cast<char*>(base) + s.off);
+}
+
+// Kernel families for profiling (names reported by mlev_profile_read).
+enum Fam {
+  F_KAPPA, F_BAND, F_LEVEL1, F_INTERP, F_RHS, F_GATHER, F_SMOOTH, F_RESTRICT, F_PROLONG, F_COARSEST, F_ACCUM,
+  F_REFINE, F_GLUE, F_STRIP_RHS, F_STRIP_UPD, F_AUG, F_RR, F_OUT, F_RESNORM, F_COUNT
+};
+const char* kFamName[F_COUNT] = {"kappa_levels", "coarse_band", "level1_lobpcg", "interp_embed", "rhs_aux",
+                                 "mg_gather", "mg_smooth", "mg_restrict", "mg_prolong", "mg_coarsest",
+                                 "mixed_accumulate", "mixed_refine_residual", "glue", "strip_rhs", "strip_update",
+                                 "aug_inner", "rayleigh_ritz", "output", "residual_check"};
+
+struct ProfRec {
+  int fam;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+struct Launcher {
+  mlev_ctx* ctx;
+  const Plan& P;
+  const mlev_opts& o;
+  void* ws;
+  cudaStream_t s;
+  DevGeom G{};
+  const double* kappa_src = nullptr;  // coarse or fine values on device (user or staged)
+  int count = 0;
+  bool profiling = false;
+  std::vector<ProfRec>* recs = nullptr;
+  std::vector<cudaEvent_t>* pool = nullptr;
+  size_t next_ev = 0;
+
+  const Tile* tiles_at(const TileList& t) const { return at<Tile>(ws, P.w_tiles) + t.off; }
+
+  cudaEvent_t ev() {
+    if (next_ev == pool->size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool->push_back(e);
+    }
+    return (*pool)[next_ev++];
+  }
+
+  // Enqueue one launch; in profiling mode bracket it with events on the stream.
+  template <class Fn>
+  void go(Fam f, double bytes, Fn&& fn) {
+    if (profiling) {
+      cudaEvent_t a = ev(), b = ev();
+      cudaEventRecord(a, s);
+      fn();
+      cudaEventRecord(b, s);
+      recs->push_back(ProfRec{f, a, b, bytes});
+    } else {
+      fn();
+    }
+    count++;
+  }
+
+  // Traffic model, bytes per unknown (t = bytes of T): see the design notes.
+  double kfine_extra() const { return P.kappa_kind == MLEV_KAPPA_PER_FINE_ELEM ? 48.0 : 0.0; }
+
+  template <typename T>
+  void vcycle(const std::vector<TileList>& lists, const TileList& coarsest, T* X, T* F) {
+    const double t = sizeof(T);
+    const int D = (int)lists.size() - 1;
+    auto smooth = [&](int d, int color) {
+      go(F_SMOOTH, (2 * t + 0.5 * kfine_extra()) * lists[d].unk,
+         [&] { launch_smooth<T>(G, tiles_at(lists[d]), lists[d].count, X, F, color, o.omega, s); });
+    };
+    for (int d = 0; d < D; ++d) {
+      for (int k = 0; k < o.pre_smooth; ++k) {
+        smooth(d, 0);
+        smooth(d, 1);
+      }
+      go(F_RESTRICT, (10 * t + 4 * kfine_extra()) * lists[d + 1].unk,
+         [&] { launch_restrict<T>(G, tiles_at(lists[d + 1]), lists[d + 1].count, X, F, s); });
+    }
+    go(F_COARSEST, 4 * t * coarsest.unk * o.coarse_sweeps,
+       [&] { launch_coarsest<T>(G, tiles_at(coarsest), coarsest.count, X, F, o.coarse_sweeps, o.omega, s); });
+    for (int d = D - 1; d >= 0; --d) {
+      go(F_PROLONG, 2.25 * t * lists[d].unk, [&] { launch_prolong<T>(G, tiles_at(lists[d]), lists[d].count, X, s); });
+      for (int k = 0; k < o.post_smooth; ++k) {
+        smooth(d, 1);
+        smooth(d, 0);
+      }
+    }
+  }
+
+  // passes of V-cycles with FP64 residual refinement in between (mixed) on one job set
+  template <typename T>
+  void solve_set(const std::vector<TileList>& lists, const TileList& coarsest, int vcycles, T* X, T* F, double* X64,
+                 const double* R) {
+    const bool mixed = sizeof(T) == 4;
+    const double t = sizeof(T);
+    const int passes = mixed ? o.refine_passes : 1;
+    const int cyc = mixed ? vcycles : vcycles * o.refine_passes;
+    const TileList& top = lists[0];
+    for (int pass = 0; pass < passes; ++pass) {
+      if (pass > 0) {
+        go(F_ACCUM, (2 * t + 16) * top.unk, [&] { launch_accumulate<T>(G, tiles_at(top), top.count, X, X64, s); });
+        go(F_REFINE, (16 + t + kfine_extra()) * top.unk,
+           [&] { launch_refine_residual<T>(G, P.glay, tiles_at(top), top.count, F, X64, R, s); });
+      }
+      for (int v = 0; v < cyc; ++v) vcycle<T>(lists, coarsest, X, F);
+    }
+    if (mixed)
+      go(F_ACCUM, (2 * t + 16) * top.unk, [&] { launch_accumulate<T>(G, tiles_at(top), top.count, X, X64, s); });
+  }
+
+  template <typename T>
+  int run(double* lambda_out, double* u_out) {
+    const int B = P.B, n = P.n;
+    const bool mixed = sizeof(T) == 4;
+    const double t = sizeof(T);
+    G.grids = at<GridDesc>(ws, P.w_grids);
+    G.regions = at<uint8_t>(ws, P.w_regions);
+    G.qlabel = at<int16_t>(ws, P.w_qlabel);
+    G.cell_in = at<uint8_t>(ws, P.w_cellin);
+    G.sub_top = at<int>(ws, P.w_subtop);
+    G.ncx = P.ncx;
+    G.ncy = P.ncy;
+    G.m = P.m;
+    G.H = P.H;
+    G.kap = P.kap_template;
+    double* klvl = at<double>(ws, P.w_klvl);
+    G.kap.lvl = klvl;
+    G.kap.coarse = P.kappa_kind == MLEV_KAPPA_PER_COARSE_CELL ? kappa_src : nullptr;
+    long long* stat = at<long long>(ws, P.w_stat);
+    const int stat_stride = mlev_stat_stride(n);
+    cudaMemsetAsync(stat, 0, P.w_stat.bytes, s);
+    double* jobnorm = at<double>(ws, P.w_jobnorm);
+    count = 0;
+    // ---- coefficient on every level, coarse pencil
+    if (P.kappa_kind == MLEV_KAPPA_PER_FINE_ELEM) {
+      go(F_KAPPA, 16.0 * B * P.lvl_nx(n) * P.lvl_ny(n) * 2,
+         [&] { launch_kappa_copy_fine(G.kap, n, B, kappa_src, klvl, s); });
+      for (int l = n - 1; l >= P.l1_lc; --l)
+        go(F_KAPPA, 40.0 * B * P.lvl_nx(l) * P.lvl_ny(l) * 2, [&] { launch_kappa_average(G.kap, l, B, klvl, s); });
+    } else if (P.kappa_kind == MLEV_KAPPA_PER_COARSE_CELL) {
+      for (int l = -1; l >= P.l1_lc; --l)
+        go(F_KAPPA, 40.0 * B * P.lvl_nx(l) * P.lvl_ny(l) * 2, [&] { launch_kappa_average(G.kap, l, B, klvl, s); });
+    }
+    double* KH = at<double>(ws, P.w_band);
+    double* MH = KH + (size_t)B * P.nhb * (P.bw + 1);
+    go(F_BAND, 16.0 * B * P.nhb * (P.bw + 1), [&] { launch_band_setup(G, B, P.nhb, P.bw, KH, MH, s); });
+    double* ut[2] = {at<double>(ws, P.w_ut[0]), at<double>(ws, P.w_ut[1])};
+    double* uin = at<double>(ws, P.w_uin);
+    double* r = at<double>(ws, P.w_r);
+    double* lam = at<double>(ws, P.w_lam);
+    double* c = at<double>(ws, P.w_c);
+    double* c0 = at<double>(ws, P.w_c0);
+    // ---- Algorithm 4.2 step 1: eigenproblem on V_{0h_1}
+    {
+      Level1Args a{};
+      a.B = B;
+      a.grid_begin = P.l1_grid_begin;
+      a.nlev = P.l1_nlev;
+      a.vec = at<double>(ws, P.w_l1vec);
+      a.vstride = P.w_l1vec.bytes / 8 / 10 / B;
+      a.xpool = at<void>(ws, P.w_l1pool[0]);
+      a.fpool = at<void>(ws, P.w_l1pool[1]);
+      a.pre = o.pre_smooth;
+      a.post = o.post_smooth;
+      a.coarse_sweeps = o.coarse_sweeps;
+      a.omega = o.omega;
+      a.max_iter = o.level1_max_iter;
+      a.tol = o.level1_tol;
+      a.ut1 = ut[1];
+      a.lam = lam;
+      a.lam_stride = n + 1;
+      a.c = c;
+      a.c0 = c0;
+      a.stat = stat;
+      a.stat_stride = stat_stride;
+      go(F_LEVEL1, 0.0, [&] { launch_level1<T>(G, P.glay, a, s); });
+    }
+    T* X = at<T>(ws, P.w_x);
+    T* F = at<T>(ws, P.w_f);
+    double* X64 = mixed ? at<double>(ws, P.w_x64) : nullptr;
+    double* partials = at<double>(ws, P.w_aug);
+    // ---- Algorithm 4.2 step 3: Correction on levels 2..n
+    for (int L = 2; L <= n; ++L) {
+      const LevelPlan& lp = P.lp[L];
+      const double nfree = (double)lp.n_free * B;
+      G.sub_top = at<int>(ws, P.w_subtop) + lp.sub_top_off;
+      LevelArgs a{};
+      a.L = L;
+      a.B = B;
+      a.ut_prev = ut[(L - 1) & 1];
+      a.ut = ut[L & 1];
+      a.uin = uin;
+      a.r = r;
+      a.c = c;
+      a.c0 = c0;
+      a.lam = lam;
+      a.lam_stride = n + 1;
+      go(F_INTERP, 10.0 * nfree, [&] { launch_interp(G, P.glay, a, s); });
+      go(F_RHS, (16.0 + kfine_extra()) * nfree, [&] { launch_rhs(G, P.glay, a, s); });
+      // step 1: auxiliary problems on every Omega_j of every batch member
+      const TileList& top = lp.sub[0];
+      go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * top.unk,
+         [&] { launch_gather<T>(G, P.glay, tiles_at(top), top.count, X, F, X64, r, s); });
+      solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, r);
+      const double* E = mixed ? X64 : reinterpret_cast<const double*>(X);
+      if (o.check_residuals) {
+        cudaMemsetAsync(jobnorm, 0, P.w_jobnorm.bytes, s);
+        go(F_RESNORM, 16.0 * top.unk,
+           [&] { launch_job_resnorm(G, P.glay, tiles_at(top), top.count, E, mixed ? 1 : 0, r, jobnorm, s); });
+        go(F_RESNORM, 0.0,
+           [&] { launch_resnorm_finalize(jobnorm, B, P.m, 1, stat, stat_stride, MLEV_STAT_LOC_RES(n) + L, s); });
+      }
+      // step 2: glue, then the G_{m+1} problem
+      go(F_GLUE, 24.0 * nfree, [&] { launch_glue(G, P.glay, a, E, mixed ? 1 : 0, s); });
+      const TileList& stop = lp.strip[0];
+      if (stop.count) {
+        go(F_STRIP_RHS, (32.0 + 2 * t + kfine_extra()) * stop.unk,
+           [&] { launch_strip_rhs<T>(G, P.glay, a, tiles_at(stop), stop.count, X, F, X64, s); });
+        solve_set<T>(lp.strip, lp.strip_coarsest, o.strip_vcycles, X, F, X64, r);
+        if (o.check_residuals) {
+          cudaMemsetAsync(jobnorm, 0, P.w_jobnorm.bytes, s);
+          go(F_RESNORM, 16.0 * stop.unk,
+             [&] { launch_job_resnorm(G, P.glay, tiles_at(stop), stop.count, E, mixed ? 1 : 0, r, jobnorm, s); });
+          go(F_RESNORM, 0.0,
+             [&] { launch_resnorm_finalize(jobnorm, B, P.m, 0, stat, stat_stride, MLEV_STAT_STRIP_RES(n) + L, s); });
+        }
+        go(F_STRIP_UPD, 24.0 * stop.unk,
+           [&] { launch_strip_update(G, P.glay, a, tiles_at(stop), stop.count, E, mixed ? 1 : 0, s); });
+      }
+      // step 3: Rayleigh-Ritz on V_{0H} + span{u~}
+      go(F_AUG, (8.0 + kfine_extra()) * nfree, [&] { launch_aug(G, P.glay, a, partials, s); });
+      RRArgs rr{};
+      rr.B = B;
+      rr.L = L;
+      rr.n = n;
+      rr.nhb = P.nhb;
+      rr.bw = P.bw;
+      rr.KH = KH;
+      rr.MH = MH;
+      rr.chol = at<double>(ws, P.w_chol);
+      rr.partials = partials;
+      rr.lam = lam;
+      rr.c = c;
+      rr.c0 = c0;
+      rr.stat = stat;
+      rr.stat_stride = stat_stride;
+      rr.max_iter = o.rr_max_iter;
+      go(F_RR, 0.0, [&] { launch_rr(G, rr, s); });
+    }
+    go(F_OUT, 16.0 * B, [&] { launch_lambda_out(B, n, lam, lambda_out, s); });
+    if (u_out)
+      go(F_OUT, 16.0 * B * (P.lvl_nx(n) + 1) * (P.lvl_ny(n) + 1),
+         [&] { launch_output_u(G, P.glay, n, B, ut[n & 1], c, c0, u_out, s); });
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    return MLEV_OK;
+  }
+};
+
+int ensure_plan(mlev_ctx* ctx, const mlev_opts* o) {
+  if (ctx->built_version == ctx->version && ctx->built_precision == o->precision) return MLEV_OK;
+  int rc = map_plan_error(ctx, ctx->plan.build(*o));
+  if (rc) return rc;
+  ctx->built_version = ctx->version;
+  ctx->built_precision = o->precision;
+  return MLEV_OK;
+}
+
+int prepare(mlev_ctx* ctx, const mlev_opts* o, void* ws, size_t ws_bytes) {
+  if (!ctx) return MLEV_EINVAL;
+  if (ctx->device < 0) return fail(ctx, MLEV_ESTATE, "planning-only context (device -1) cannot solve");
+  if (!opts_valid(o)) return fail(ctx, MLEV_EINVAL, "invalid options");
+  int rc = ensure_plan(ctx, o);
+  if (rc) return rc;
+  ctx->io_h2d = ctx->io_d2h = 0;
+  if (!ws || ((uintptr_t)ws & 255)) return fail(ctx, MLEV_EINVAL, "workspace must be non-NULL and 256-byte aligned");
+  if (ws_bytes < ctx->plan.ws_bytes)
+    return fail(ctx, MLEV_ENOMEM, "workspace too small: need " + std::to_string(ctx->plan.ws_bytes) + " bytes");
+  return MLEV_OK;
+}
+
+int upload_tables(mlev_ctx* ctx, void* ws, cudaStream_t s, bool force) {
+  Plan& P = ctx->plan;
+  const long long key = ctx->version * 2 + ctx->built_precision;
+  if (!force && ctx->uploaded_ws == ws && ctx->uploaded_version == key) return MLEV_OK;
+  std::vector<char> host(P.tables_bytes, 0);
+  auto put = [&](const Span& sp, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(host.data() + sp.off, src, bytes);
+  };
+  put(P.w_grids, P.grids.data(), P.grids.size() * sizeof(GridDesc));
+  put(P.w_tiles, P.tiles.data(), P.tiles.size() * sizeof(Tile));
+  put(P.w_regions, P.regions.data(), P.regions.size());
+  put(P.w_qlabel, P.qlabel.data(), P.qlabel.size() * sizeof(int16_t));
+  put(P.w_cellin, P.cell_in.data(), P.cell_in.size());
+  put(P.w_subtop, P.sub_top.data(), P.sub_top.size() * sizeof(int));
+  CK(cudaMemcpyAsync(ws, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+  ctx->io_h2d += (long long)host.size();
+  if (!P.kappa_on_device && !P.kappa_host.empty()) {
+    CK(cudaMemcpyAsync(at<char>(ws, P.w_kstage), P.kappa_host.data(), P.kappa_host.size() * 8,
+                       cudaMemcpyHostToDevice, s));
+    ctx->io_h2d += (long long)P.kappa_host.size() * 8;
+  }
+  CK(cudaStreamSynchronize(s));
+  ctx->uploaded_ws = ws;
+  ctx->uploaded_version = key;
+  ctx->kappa_dirty = false;
+  return MLEV_OK;
+}
+
+int fill_report(mlev_ctx* ctx, void* ws, cudaStream_t s, mlev_report* rep) {
+  const Plan& P = ctx->plan;
+  CK(cudaStreamSynchronize(s));
+  const int n = P.n, B = P.B, stride = mlev_stat_stride(n);
+  std::vector<long long> st((size_t)B * stride);
+  std::vector<double> lam((size_t)B * (n + 1));
+  CK(cudaMemcpy(st.data(), at<char>(ws, P.w_stat), st.size() * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(lam.data(), at<char>(ws, P.w_lam), lam.size() * 8, cudaMemcpyDeviceToHost));
+  std::memset(rep, 0, sizeof(*rep));
+  rep->levels = n;
+  rep->batch = B;
+  for (int k = 1; k <= n; ++k) rep->lambda[k] = lam[k];
+  int flags = 0;
+  for (int b = 0; b < B; ++b) {
+    const long long* sb = st.data() + (size_t)b * stride;
+    auto as_double = [](long long v) {
+      double d;
+      std::memcpy(&d, &v, 8);
+      return d;
+    };
+    rep->level1_iters = std::max(rep->level1_iters, (int)sb[MLEV_STAT_L1_IT]);
+    rep->level1_residual = std::max(rep->level1_residual, as_double(sb[MLEV_STAT_L1_RES]));
+    flags |= (int)sb[MLEV_STAT_FLAGS];
+    for (int k = 2; k <= n; ++k) {
+      rep->rr_iters[k] = std::max(rep->rr_iters[k], (int)sb[MLEV_STAT_RR_IT + k]);
+      rep->local_residual[k] = std::max(rep->local_residual[k], as_double(sb[MLEV_STAT_LOC_RES(n) + k]));
+      rep->strip_residual[k] = std::max(rep->strip_residual[k], as_double(sb[MLEV_STAT_STRIP_RES(n) + k]));
+    }
+  }
+  rep->status_flags = flags;
+  rep->n_fine = P.n_fine;
+  rep->n_local_fine = P.lp[n].n_local;
+  rep->n_strip_fine = P.lp[n].n_strip;
+  rep->n_coarse = P.n_coarse;
+  rep->kernel_launches = ctx->launches;
+  rep->h2d_bytes = ctx->io_h2d;
+  rep->d2h_bytes = ctx->io_d2h;
+  if (flags & (MLEV_ST_LEVEL1_NOCONV | MLEV_ST_RR_NOCONV))
+    return fail(ctx, MLEV_ENOCONV, "an iteration reached its cap (status flags " + std::to_string(flags) + ")");
+  if (flags) return fail(ctx, MLEV_ENOCONV, "numerical breakdown (status flags " + std::to_string(flags) + ")");
+  return MLEV_OK;
+}
+
+int solve_impl(mlev_ctx* ctx, const mlev_opts* o, void* ws, size_t ws_bytes, cudaStream_t s,
+               const double* kappa_src, double* lambda_out, double* u_out) {
+  const Plan& P = ctx->plan;
+  Launcher ln{ctx, P, *o, ws, s};
+  ln.kappa_src = kappa_src;
+  int rc;
+  if (o->profile) {
+    std::vector<ProfRec> recs;
+    ln.profiling = true;
+    ln.recs = &recs;
+    ln.pool = &ctx->ev_pool;
+    rc = o->precision == MLEV_PREC_FP64 ? ln.run<double>(lambda_out, u_out) : ln.run<float>(lambda_out, u_out);
+    ctx->launches = ln.count;
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s));
+    ctx->prof.assign(F_COUNT, ProfRecHost());
+    for (const ProfRec& r : recs) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, r.a, r.b));
+      ctx->prof[r.fam].launches++;
+      ctx->prof[r.fam].ms += ms;
+      ctx->prof[r.fam].bytes += r.bytes;
+    }
+    ctx->prof_valid = true;
+    return MLEV_OK;
+  }
+  if (o->use_graph) {
+    char key[256];
+    snprintf(key, sizeof key, "%p/%p/%p/%p/%p/%lld/", ws, (void*)s, (void*)lambda_out, (void*)u_out,
+             (const void*)kappa_src, ctx->version);
+    const std::string k = std::string(key) + opts_key(o);
+    if (!ctx->gexec || ctx->graph_key != k) {
+      if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+      }
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      rc = o->precision == MLEV_PREC_FP64 ? ln.run<double>(lambda_out, u_out) : ln.run<float>(lambda_out, u_out);
+      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      if (rc) return rc;
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+      ctx->graph_key = k;
+      ctx->graph_launches = ln.count;
+    }
+    CK(cudaGraphLaunch(ctx->gexec, s));
+    ctx->launches = ctx->graph_launches;
+    return MLEV_OK;
+  }
+  rc = o->precision == MLEV_PREC_FP64 ? ln.run<double>(lambda_out, u_out) : ln.run<float>(lambda_out, u_out);
+  ctx->launches = ln.count;
+  return rc;
+}
+
+const double* kappa_device_src(mlev_ctx* ctx, void* ws) {
+  const Plan& P = ctx->plan;
+  if (P.kappa_kind == MLEV_KAPPA_ONE) return nullptr;
+  if (P.kappa_on_device) return P.kappa_dev;
+  return at<double>(ws, P.w_kstage);
+}
+
+}  // namespace
+
+extern "C" {
+
+void mlev_opts_default(mlev_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = MLEV_PREC_MIXED;
+  o->vcycles = 4;
+  o->refine_passes = 2;
+  o->strip_vcycles = 4;
+  o->pre_smooth = 2;
+  o->post_smooth = 2;
+  o->coarse_sweeps = 40;
+  o->level1_max_iter = 60;
+  o->level1_tol = 1e-10;
+  o->rr_max_iter = 100;
+  o->use_graph = 0;
+  o->omega = 1.0;
+  o->check_residuals = 0;
+}
+
+int mlev_create(mlev_ctx** out, int device) {
+  if (!out) return MLEV_EINVAL;
+  *out = nullptr;
+  if (device == -1) {  // planning-only context: set-up, validation and sizes, no solves
+    mlev_ctx* c = new (std::nothrow) mlev_ctx();
+    if (!c) return MLEV_ENOMEM;
+    c->device = -1;
+    *out = c;
+    return MLEV_OK;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MLEV_ECUDA;
+  mlev_ctx* c = new (std::nothrow) mlev_ctx();
+  if (!c) return MLEV_ENOMEM;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return MLEV_ECUDA;
+  }
+  *out = c;
+  return MLEV_OK;
+}
+
+void mlev_destroy(mlev_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* mlev_last_error(const mlev_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int mlev_set_domain(mlev_ctx* ctx, int ncx, int ncy, double x0, double y0, double H, const uint8_t* cell_in) {
+  if (!ctx) return MLEV_EINVAL;
+  if (ncx < 2 || ncy < 2 || ncx > 64 || ncy > 64 || !(H > 0) || !cell_in)
+    return fail(ctx, MLEV_EINVAL, "domain: need 2 <= ncx, ncy <= 64, H > 0 and a cell mask");
+  Plan& P = ctx->plan;
+  P.ncx = ncx;
+  P.ncy = ncy;
+  P.x0 = x0;
+  P.y0 = y0;
+  P.H = H;
+  P.cell_in.assign(cell_in, cell_in + (size_t)ncx * ncy);
+  for (auto& v : P.cell_in) v = v ? 1 : 0;
+  bool any = false;
+  for (auto v : P.cell_in) any = any || v;
+  if (!any) return fail(ctx, MLEV_EINVAL, "domain has no cell");
+  P.has_domain = true;
+  P.has_partition = false;
+  ctx->version++;
+  return MLEV_OK;
+}
+
+int mlev_set_partition(mlev_ctx* ctx, int m, const int32_t* owner, const int32_t* overlap, double delta,
+                       int glue_mode) {
+  if (!ctx) return MLEV_EINVAL;
+  Plan& P = ctx->plan;
+  if (!P.has_domain) return fail(ctx, MLEV_ESTATE, "set the domain first");
+  if (m < 1 || !owner || !overlap) return fail(ctx, MLEV_EINVAL, "partition: need m >= 1, cell_owner and overlap");
+  if (glue_mode != MLEV_GLUE_PAPER) return fail(ctx, MLEV_EUNSUPPORTED, "only MLEV_GLUE_PAPER is implemented");
+  P.m = m;
+  P.owner.assign(owner, owner + (size_t)P.ncx * P.ncy);
+  P.overlap.assign(overlap, overlap + m);
+  P.delta = delta;
+  P.glue_mode = glue_mode;
+  std::string e = check_partition(P);
+  int rc = map_plan_error(ctx, e);
+  if (rc) return rc;
+  P.has_partition = true;
+  ctx->version++;
+  return MLEV_OK;
+}
+
+int mlev_set_levels(mlev_ctx* ctx, int n) {
+  if (!ctx) return MLEV_EINVAL;
+  if (n < 2 || n > MLEV_MAX_LEVELS) return fail(ctx, MLEV_EINVAL, "levels: need 2 <= n <= MLEV_MAX_LEVELS");
+  Plan& P = ctx->plan;
+  if (P.has_forms && P.kappa_kind == MLEV_KAPPA_PER_FINE_ELEM && P.n != n) P.has_forms = false;
+  P.n = n;
+  P.has_levels = true;
+  ctx->version++;
+  return MLEV_OK;
+}
+
+int mlev_set_forms(mlev_ctx* ctx, int batch, int kappa_kind, const double* kappa, int kappa_on_device) {
+  if (!ctx) return MLEV_EINVAL;
+  Plan& P = ctx->plan;
+  if (batch < 1) return fail(ctx, MLEV_EINVAL, "batch must be >= 1");
+  if (kappa_kind < MLEV_KAPPA_ONE || kappa_kind > MLEV_KAPPA_PER_FINE_ELEM)
+    return fail(ctx, MLEV_EINVAL, "unknown kappa kind");
+  if (kappa_kind != MLEV_KAPPA_ONE && !kappa) return fail(ctx, MLEV_EINVAL, "kappa values required");
+  if (!P.has_domain) return fail(ctx, MLEV_ESTATE, "set the domain first");
+  if (kappa_kind == MLEV_KAPPA_PER_FINE_ELEM && !P.has_levels)
+    return fail(ctx, MLEV_ESTATE, "set the levels before per-element kappa");
+  P.B = batch;
+  P.kappa_kind = kappa_kind;
+  P.kappa_on_device = kappa_on_device != 0;
+  P.kappa_dev = P.kappa_on_device ? kappa : nullptr;
+  P.kappa_host.clear();
+  if (kappa_kind != MLEV_KAPPA_ONE && !P.kappa_on_device) {
+    size_t cnt = kappa_kind == MLEV_KAPPA_PER_COARSE_CELL
+                     ? (size_t)batch * P.ncx * P.ncy
+                     : (size_t)batch * ((size_t)P.ncx << P.n) * ((size_t)P.ncy << P.n) * 2;
+    P.kappa_host.assign(kappa, kappa + cnt);
+    for (size_t i = 0; i < cnt; ++i)
+      if (!(P.kappa_host[i] >= 0) || !std::isfinite(P.kappa_host[i]))
+        return fail(ctx, MLEV_EINVAL, "kappa must be finite and non-negative");
+  }
+  P.has_forms = true;
+  ctx->version++;
+  ctx->kappa_dirty = true;
+  return MLEV_OK;
+}
+
+int mlev_workspace_size(mlev_ctx* ctx, const mlev_opts* opts, size_t* bytes) {
+  if (!ctx || !bytes) return MLEV_EINVAL;
+  if (!opts_valid(opts)) return fail(ctx, MLEV_EINVAL, "invalid options");
+  int rc = ensure_plan(ctx, opts);
+  if (rc) return rc;
+  *bytes = ctx->plan.ws_bytes;
+  return MLEV_OK;
+}
+
+int mlev_problem_info(mlev_ctx* ctx, long long* n_fine, long long* n_local_fine, long long* n_strip_fine,
+                      int* n_coarse) {
+  if (!ctx) return MLEV_EINVAL;
+  mlev_opts o;
+  mlev_opts_default(&o);
+  if (ctx->built_precision >= 0) o.precision = ctx->built_precision;
+  int rc = ensure_plan(ctx, &o);
+  if (rc) return rc;
+  const Plan& P = ctx->plan;
+  if (n_fine) *n_fine = P.n_fine;
+  if (n_local_fine) *n_local_fine = P.lp[P.n].n_local;
+  if (n_strip_fine) *n_strip_fine = P.lp[P.n].n_strip;
+  if (n_coarse) *n_coarse = P.n_coarse;
+  return MLEV_OK;
+}
+
+int mlev_solve(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
+               double* lambda_out, double* u_out, mlev_report* rep) {
+  int rc = prepare(ctx, opts, workspace, ws_bytes);
+  if (rc) return rc;
+  if (!lambda_out) return fail(ctx, MLEV_EINVAL, "lambda_out is required");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, MLEV_ECUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = upload_tables(ctx, workspace, s, false);
+  if (rc) return rc;
+  rc = solve_impl(ctx, opts, workspace, ws_bytes, s, kappa_device_src(ctx, workspace), lambda_out, u_out);
+  if (rc) return rc;
+  if (rep) return fill_report(ctx, workspace, s, rep);
+  return MLEV_OK;
+}
+
+int mlev_solve_host(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
+                    const double* kappa_host, double* lambda_host, double* u_host, mlev_report* rep) {
+  int rc = prepare(ctx, opts, workspace, ws_bytes);
+  if (rc) return rc;
+  if (!lambda_host) return fail(ctx, MLEV_EINVAL, "lambda_host is required");
+  const Plan& P = ctx->plan;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, MLEV_ECUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = upload_tables(ctx, workspace, s, true);
+  if (rc) return rc;
+  const double* ksrc = kappa_device_src(ctx, workspace);
+  if (kappa_host && P.kappa_kind != MLEV_KAPPA_ONE) {
+    CK(cudaMemcpyAsync(at<char>(workspace, P.w_kstage), kappa_host, P.w_kstage.bytes, cudaMemcpyHostToDevice, s));
+    ctx->io_h2d += (long long)P.w_kstage.bytes;
+    ksrc = at<double>(workspace, P.w_kstage);
+  }
+  double* dlam = at<double>(workspace, P.w_out_lam);
+  double* du = u_host ? at<double>(workspace, P.w_out_u) : nullptr;
+  rc = solve_impl(ctx, opts, workspace, ws_bytes, s, ksrc, dlam, du);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(lambda_host, dlam, (size_t)P.B * 8, cudaMemcpyDeviceToHost, s));
+  ctx->io_d2h += (long long)P.B * 8;
+  if (u_host) {
+    const size_t ub = (size_t)P.B * (P.lvl_nx(P.n) + 1) * (P.lvl_ny(P.n) + 1) * 8;
+    CK(cudaMemcpyAsync(u_host, du, ub, cudaMemcpyDeviceToHost, s));
+    ctx->io_d2h += (long long)ub;
+  }
+  CK(cudaStreamSynchronize(s));
+  if (rep) return fill_report(ctx, workspace, s, rep);
+  return MLEV_OK;
+}
+
+}  // extern "C"
+
+extern "C" int mlev_profile_read(mlev_ctx* ctx, mlev_kernel_stat* out, int capacity, int* count) {
+  if (!ctx) return MLEV_EINVAL;
+  if (!ctx->prof_valid) return fail(ctx, MLEV_ESTATE, "no profiled solve has completed");
+  if (count) *count = F_COUNT;
+  for (int i = 0; i < F_COUNT && i < capacity && out; ++i) {
+    std::memset(&out[i], 0, sizeof(out[i]));
+    std::snprintf(out[i].name, sizeof(out[i].name), "%s", kFamName[i]);
+    out[i].launches = ctx->prof[i].launches;
+    out[i].ms = ctx->prof[i].ms;
+    out[i].bytes = ctx->prof[i].bytes;
+  }
+  return MLEV_OK;
+}

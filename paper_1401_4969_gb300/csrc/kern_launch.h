@@ -1,0 +1,103 @@
+// Host-callable launchers of the device kernels (one per kernel family). Every
+// launcher enqueues on the given stream and never synchronizes.
+#pragma once
+
+#include "kern_common.cuh"
+
+namespace mlev {
+
+// ---- multigrid (kern_mg.cu), T = float (mixed) or double (plain FP64) ----
+template <typename T>
+void launch_smooth(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, int color, double omega,
+                   cudaStream_t s);
+template <typename T>
+void launch_restrict(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, cudaStream_t s);
+template <typename T>
+void launch_prolong(const DevGeom& G, const Tile* tiles, int n, T* X, cudaStream_t s);
+template <typename T>
+void launch_coarsest(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, int sweeps, double omega,
+                     cudaStream_t s);
+void launch_job_resnorm(const DevGeom& G, const GlobalLayout& gl, const Tile* tiles, int n, const double* E, int use64,
+                        const double* R, double* acc, cudaStream_t s);
+void launch_resnorm_finalize(const double* acc, int B, int m, int subdomains, long long* stat, int stat_stride,
+                             int slot, cudaStream_t s);
+template <typename T>
+void launch_gather(const DevGeom& G, const GlobalLayout& gl, const Tile* tiles, int n, T* X, T* F, double* X64,
+                   const double* R, cudaStream_t s);
+template <typename T>
+void launch_accumulate(const DevGeom& G, const Tile* tiles, int n, T* X, double* X64, cudaStream_t s);
+template <typename T>
+void launch_refine_residual(const DevGeom& G, const GlobalLayout& gl, const Tile* tiles, int n, T* F,
+                            const double* X64, const double* R, cudaStream_t s);
+
+// ---- global fields (kern_field.cu) ----
+struct LevelArgs {
+  int L;                 // current level
+  int B;
+  const double* ut_prev; // u~ on level L-1 (pitched, level L-1 layout)
+  double* ut;            // u~ on level L
+  double* uin;           // u_{h_k} embedded in V_{h_L}
+  double* r;             // residual / right-hand side field
+  const double* c;       // [B][(ncy+1)(ncx+1)] coarse coefficients of u_{h_k}
+  const double* c0;      // [B] coefficient of u~ in u_{h_k}
+  const double* lam;     // [B][n+1] eigenvalue per level
+  int lam_stride;        // n + 1
+};
+void launch_interp(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, cudaStream_t s);
+void launch_rhs(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, cudaStream_t s);
+// glue: E = FP64 local solutions (pool base); use64 selects GridDesc::off64 (mixed) or ::off (FP64 mode)
+void launch_glue(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const double* E, int use64,
+                 cudaStream_t s);
+template <typename T>
+void launch_strip_rhs(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const Tile* tiles, int n, T* X,
+                      T* F, double* X64, cudaStream_t s);
+void launch_strip_update(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const Tile* tiles, int n,
+                         const double* E, int use64, cudaStream_t s);
+void launch_aug(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, double* partials, cudaStream_t s);
+void launch_output_u(const DevGeom& G, const GlobalLayout& gl, int L, int B, const double* ut, const double* c,
+                     const double* c0, double* u_out, cudaStream_t s);
+void launch_kappa_copy_fine(const KappaDev& kv, int n, int B, const double* src, double* lvl, cudaStream_t s);
+void launch_kappa_average(const KappaDev& kv, int l, int B, double* lvl, cudaStream_t s);
+void launch_band_setup(const DevGeom& G, int B, int nhb, int bw, double* KH, double* MH, cudaStream_t s);
+void launch_lambda_out(int B, int n, const double* lam, double* out, cudaStream_t s);
+
+// ---- eigen solvers (kern_eig.cu) ----
+struct Level1Args {
+  int B;
+  int grid_begin, nlev;  // level-1 job grids of problem b: grid_begin + b * nlev + depth
+  double* vec;           // 10 FP64 vectors per problem, each vstride elements
+  long long vstride;     // elements per vector (per problem); problem b at vec + b * 10 * vstride
+  void* xpool;           // multigrid pools (T)
+  void* fpool;
+  int pre, post, coarse_sweeps;
+  double omega;
+  int max_iter;
+  double tol;
+  double* ut1;           // output u~_1 = u_{h_1} on level 1, global layout
+  double* lam;           // [B][n+1]: writes index 1
+  int lam_stride;
+  double* c;             // zeroed coarse coefficients
+  double* c0;            // set to 1
+  long long* stat;       // [B][...] iterations, residual bits
+  int stat_stride;
+};
+template <typename T>
+void launch_level1(const DevGeom& G, const GlobalLayout& gl, const Level1Args& a, cudaStream_t s);
+
+struct RRArgs {
+  int B, L, n;
+  int nhb, bw;
+  const double* KH;
+  const double* MH;
+  double* chol;          // [B][nhb][bw+1] scratch
+  const double* partials;
+  double* lam;           // [B][n+1]
+  double* c;             // [B][(ncy+1)(ncx+1)]
+  double* c0;            // [B]
+  long long* stat;
+  int stat_stride;
+  int max_iter;
+};
+void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s);
+
+}  // namespace mlev

@@ -1,0 +1,79 @@
+// Internal data structures shared by the host planner (plan.cpp), the kernels and
+// the C-ABI layer. Plain old data only, so the same structs live in host and device
+// memory.
+#pragma once
+
+#include <stdint.h>
+
+#define MLEV_MAX_TOTAL_LEVELS 16  // level-1 job may coarsen below T_H; absolute levels in [-6, 10]
+#define MLEV_LMIN (-6)
+
+// One grid of one multigrid job at one level. A job is a rectangular window of the
+// level-l lattice (a subdomain Omega_j, the strip G_{m+1}, or the whole domain for the
+// level-1 eigenproblem) together with a region mask that says which interior nodes
+// are unknowns.
+struct GridDesc {
+  int nx, ny;        // cells; nodes 0..nx x 0..ny, the outer ring is never an unknown
+  int pitch;         // row pitch in elements
+  int ox, oy;        // lattice coordinates of node (0,0) in the global level-`level` lattice
+  int level;         // absolute level (mesh size H / 2^level), may be negative
+  int problem;       // batch member
+  int full;          // 1: every strictly interior node is an unknown (no region lookups)
+  int rshift;        // level - (level of the region grid)
+  int rnx, rny;      // region grid size in region cells
+  int job;           // owning job
+  int depth;         // 0 = finest grid of the job
+  long long roff;    // byte offset of the region grid in the region pool
+  long long off;     // element offset of node (0,0) in the X / F pools
+  long long off64;   // element offset in the FP64 pools (finest grid only, else -1)
+};
+
+struct Tile {  // a block of nodes of one grid: origin (x0, y0), size fixed by the kernel
+  int grid;
+  int x0, y0;
+};
+
+// Device view of the coefficient kappa.
+struct KappaDev {
+  int kind;                          // MLEV_KAPPA_*
+  int ncx, ncy;                      // T_H
+  const double* coarse;              // kind PER_COARSE_CELL: [B][ncy][ncx]
+  const double* lvl;                 // per-level triangle values (kinds 1 with level<0, and 2)
+  long long lvl_off[MLEV_MAX_TOTAL_LEVELS];     // element offset of level (l - MLEV_LMIN)
+  long long lvl_bstride[MLEV_MAX_TOTAL_LEVELS]; // elements per batch member at that level
+};
+
+// Everything a kernel needs to interpret grids.
+struct DevGeom {
+  const GridDesc* grids;
+  const uint8_t* regions;   // region pool
+  const int16_t* qlabel;    // [4*ncy][4*ncx]: -1 outside Omega, 0 strip, j+1 inside G_j
+  const uint8_t* cell_in;   // [ncy][ncx]
+  const int* sub_top;       // [B*m] grid index of the finest grid of subdomain j of problem b (current level)
+  int ncx, ncy, m;
+  double H;
+  KappaDev kap;
+};
+
+// Global per-level field layout (per batch member): rows 0..NY_l, pitch gpitch[l].
+struct GlobalLayout {
+  int nx[MLEV_MAX_TOTAL_LEVELS];      // cells at level l (index l - MLEV_LMIN)
+  int ny[MLEV_MAX_TOTAL_LEVELS];
+  int pitch[MLEV_MAX_TOTAL_LEVELS];
+  long long bstride;                  // elements per batch member (sized for the finest level)
+};
+
+// Device status bits.
+#define MLEV_ST_LEVEL1_NOCONV 1
+#define MLEV_ST_RR_NOCONV 2
+#define MLEV_ST_RR_BREAKDOWN 4
+#define MLEV_ST_NONFINITE 8
+
+// Per-problem status record (long long slots), stride mlev_stat_stride(n).
+#define MLEV_STAT_L1_IT 0     // level-1 iterations
+#define MLEV_STAT_L1_RES 1    // level-1 final relative residual (double bits)
+#define MLEV_STAT_FLAGS 2     // MLEV_ST_* bits
+#define MLEV_STAT_RR_IT 4     // + L: Rayleigh-Ritz iterations on level L
+#define MLEV_STAT_LOC_RES(n) (4 + ((n) + 1))        // + L: max relative residual of the local solves
+#define MLEV_STAT_STRIP_RES(n) (4 + 2 * ((n) + 1))  // + L: relative residual of the G_{m+1} solve
+static inline int mlev_stat_stride(int n) { return 4 + 3 * (n + 1); }

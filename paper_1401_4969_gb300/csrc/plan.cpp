@@ -1,0 +1,445 @@
+// Host planner: decomposition sets of Section 4 and the workspace layout.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace mlev {
+
+namespace {
+
+constexpr int kTX = 32;  // node tile width used by every tiled kernel
+constexpr int kTY = 8;   // node tile height
+constexpr int kAlignElems = 32;
+
+long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+int pitch_for(int nodes) { return (int)round_up(nodes, kAlignElems); }
+
+}  // namespace
+
+// D_j must be rectangles; computes D, Omega_j (Chebyshev dilation by o_j, clipped
+// to the grid and intersected with Omega) and the closed G_j as quarter-lattice
+// rectangles, then labels every quarter cell.
+std::string check_partition(Plan& p) {
+  const int ncx = p.ncx, ncy = p.ncy;
+  p.D.assign(p.m, {ncx, ncy, -1, -1});
+  std::vector<int> count(p.m, 0);
+  for (int cj = 0; cj < ncy; ++cj)
+    for (int ci = 0; ci < ncx; ++ci) {
+      int j = p.owner[cj * ncx + ci];
+      bool in = p.cell_in[cj * ncx + ci] != 0;
+      if (!in) {
+        if (j != -1) return "cell_owner must be -1 on cells outside Omega";
+        continue;
+      }
+      if (j < 0 || j >= p.m) return "cell_owner out of range on a cell of Omega";
+      auto& r = p.D[j];
+      r[0] = std::min(r[0], ci);
+      r[1] = std::min(r[1], cj);
+      r[2] = std::max(r[2], ci + 1);
+      r[3] = std::max(r[3], cj + 1);
+      count[j]++;
+    }
+  for (int j = 0; j < p.m; ++j) {
+    auto& r = p.D[j];
+    if (count[j] == 0) return "subdomain " + std::to_string(j) + " owns no cell";
+    if (count[j] != (r[2] - r[0]) * (r[3] - r[1]))
+      return "UNSUPPORTED: subdomain " + std::to_string(j) + " is not a rectangle of cells";
+    if (p.overlap[j] < 0) return "overlap must be >= 0";
+  }
+  const double dq = p.delta / (0.25 * p.H);
+  const int d = (int)std::lround(dq);
+  if (!(p.delta > 0) || std::fabs(dq - d) > 1e-9 * std::max(1.0, dq))
+    return "delta must be a positive multiple of H/4";
+  auto inside = [&](int ci, int cj) {
+    return ci >= 0 && cj >= 0 && ci < ncx && cj < ncy && p.cell_in[cj * ncx + ci] != 0;
+  };
+  p.Om.resize(p.m);
+  p.G.resize(p.m);
+  for (int j = 0; j < p.m; ++j) {
+    auto r = p.D[j];
+    int o = p.overlap[j];
+    p.Om[j] = {std::max(0, r[0] - o), std::max(0, r[1] - o), std::min(ncx, r[2] + o), std::min(ncy, r[3] + o)};
+    // a side of D_j is part of dD_j \ dOmega where the cell across it is in Omega
+    auto side = [&](int fixed_c, int lo, int hi, bool vertical) {
+      int cnt = 0;
+      for (int t = lo; t < hi; ++t) cnt += vertical ? inside(fixed_c, t) : inside(t, fixed_c);
+      return cnt == 0 ? 0 : (cnt == hi - lo ? 1 : -1);
+    };
+    int sl = side(r[0] - 1, r[1], r[3], true), sr = side(r[2], r[1], r[3], true);
+    int sb = side(r[1] - 1, r[0], r[2], false), st = side(r[3], r[0], r[2], false);
+    if (sl < 0 || sr < 0 || sb < 0 || st < 0)
+      return "UNSUPPORTED: a side of D_" + std::to_string(j) + " is partly on dOmega";
+    std::array<int, 4> g = {4 * r[0] + (sl ? d : 0), 4 * r[1] + (sb ? d : 0), 4 * r[2] - (sr ? d : 0),
+                            4 * r[3] - (st ? d : 0)};
+    if (g[0] >= g[2] || g[1] >= g[3]) return "delta too large: G_" + std::to_string(j) + " is empty";
+    p.G[j] = g;
+  }
+  // quarter-cell labels
+  const int qx = 4 * ncx, qy = 4 * ncy;
+  p.qlabel.assign((size_t)qx * qy, 0);
+  for (int y = 0; y < qy; ++y)
+    for (int x = 0; x < qx; ++x) {
+      int16_t lab = inside(x >> 2, y >> 2) ? 0 : -1;
+      if (lab == 0)
+        for (int j = 0; j < p.m; ++j) {
+          const auto& g = p.G[j];
+          if (x >= g[0] && x + 1 <= g[2] && y >= g[1] && y + 1 <= g[3]) {
+            if (lab != 0) return "closed G_j overlap";
+            lab = (int16_t)(j + 1);
+          }
+        }
+      p.qlabel[(size_t)y * qx + x] = lab;
+    }
+  // closed G_j must be disjoint also on their boundaries (checked on the quarter lattice)
+  for (int i = 0; i < p.m; ++i)
+    for (int j = i + 1; j < p.m; ++j) {
+      const auto &a = p.G[i], &b = p.G[j];
+      if (a[0] <= b[2] && b[0] <= a[2] && a[1] <= b[3] && b[1] <= a[3]) return "closed G_j overlap";
+    }
+  return "";
+}
+
+// Host replica of the device unknown test, summed over one grid.
+long long grid_unknowns(const Plan& p, const GridDesc& g) {
+  if (g.full) return (long long)(g.nx - 1) * (g.ny - 1);
+  long long cnt = 0;
+  const uint8_t* reg = p.regions.data() + g.roff;
+  const int s = g.rshift;
+  for (int j = 1; j < g.ny; ++j)
+    for (int i = 1; i < g.nx; ++i) {
+      const int a = (i - 1) >> s, b = i >> s, c = (j - 1) >> s, d = j >> s;
+      cnt += reg[c * g.rnx + a] && reg[c * g.rnx + b] && reg[d * g.rnx + a] && reg[d * g.rnx + b];
+    }
+  return cnt;
+}
+
+std::string Plan::build(const mlev_opts& o) {
+  if (!ready()) return "STATE: set domain, partition, levels and forms before solving";
+  tsize = o.precision == MLEV_PREC_FP64 ? 8 : 4;
+  std::string err = check_partition(*this);
+  if (!err.empty()) return err;
+
+  // ---- level-1 hierarchy depth: coarsen T_H while the cell mask stays block-aligned ----
+  l1_lc = 0;
+  for (int s = 1; s <= -MLEV_LMIN; ++s) {
+    int b = 1 << s;
+    if (ncx % b || ncy % b || ncx / b < 2 || ncy / b < 2) break;
+    bool ok = true;
+    for (int cj = 0; cj < ncy && ok; ++cj)
+      for (int ci = 0; ci < ncx && ok; ++ci)
+        ok = cell_in[cj * ncx + ci] == cell_in[(cj & ~(b - 1)) * ncx + (ci & ~(b - 1))];
+    if (!ok) break;
+    // the coarsest grid must keep at least one unknown
+    int cx = ncx / b, cy = ncy / b, unk = 0;
+    for (int y = 1; y < cy; ++y)
+      for (int x = 1; x < cx; ++x) {
+        bool all = true;
+        for (int dy = -1; dy <= 0; ++dy)
+          for (int dx = -1; dx <= 0; ++dx) all = all && cell_in[((y + dy) * b) * ncx + (x + dx) * b];
+        unk += all;
+      }
+    if (!unk) break;
+    l1_lc = -s;
+  }
+
+  // ---- global layout ----
+  std::memset(&glay, 0, sizeof(glay));
+  for (int l = l1_lc; l <= n; ++l) {
+    int i = l - MLEV_LMIN;
+    glay.nx[i] = l >= 0 ? ncx << l : ncx >> (-l);
+    glay.ny[i] = l >= 0 ? ncy << l : ncy >> (-l);
+    glay.pitch[i] = pitch_for(glay.nx[i] + 1);
+  }
+  glay.bstride = round_up((long long)(lvl_ny(n) + 1) * lvl_pitch(n), 64);
+  {
+    long long nf = 0;
+    const int nxn = lvl_nx(n), nyn = lvl_ny(n), s = n;
+    for (int y = 1; y < nyn; ++y)
+      for (int x = 1; x < nxn; ++x) {
+        bool all = true;
+        for (int dy = -1; dy <= 0 && all; ++dy)
+          for (int dx = -1; dx <= 0 && all; ++dx) all = cell_in[((y + dy) >> s) * ncx + ((x + dx) >> s)] != 0;
+        nf += all;
+      }
+    n_fine = nf;
+    int nc = 0;
+    for (int y = 1; y < ncy; ++y)
+      for (int x = 1; x < ncx; ++x)
+        nc += cell_in[y * ncx + x] && cell_in[(y - 1) * ncx + x] && cell_in[y * ncx + x - 1] &&
+              cell_in[(y - 1) * ncx + x - 1];
+    n_coarse = nc;
+  }
+  nhb = (ncx - 1) * (ncy - 1);
+  bw = ncx;
+
+  // ---- region grids ----
+  regions.clear();
+  auto add_region = [&](const std::vector<uint8_t>& r) {
+    long long off = (long long)regions.size();
+    regions.insert(regions.end(), r.begin(), r.end());
+    while (regions.size() % 16) regions.push_back(0);
+    return off;
+  };
+  std::vector<long long> sub_roff(m);
+  std::vector<int> sub_full(m);
+  for (int j = 0; j < m; ++j) {
+    const auto& r = Om[j];
+    std::vector<uint8_t> reg;
+    bool full = true;
+    for (int cj = r[1]; cj < r[3]; ++cj)
+      for (int ci = r[0]; ci < r[2]; ++ci) {
+        reg.push_back(cell_in[cj * ncx + ci] ? 1 : 0);
+        full = full && cell_in[cj * ncx + ci];
+      }
+    sub_roff[j] = add_region(reg);
+    sub_full[j] = full;
+  }
+  std::vector<uint8_t> sreg(qlabel.size());
+  for (size_t i = 0; i < qlabel.size(); ++i) sreg[i] = qlabel[i] == 0;
+  const long long strip_roff = add_region(sreg);
+  std::vector<uint8_t> l1reg;
+  {
+    int b = 1 << (-l1_lc);
+    for (int y = 0; y < ncy / b; ++y)
+      for (int x = 0; x < ncx / b; ++x) l1reg.push_back(cell_in[(y * b) * ncx + x * b] ? 1 : 0);
+  }
+  const long long l1_roff = add_region(l1reg);
+  bool dom_full = true;
+  for (auto c : cell_in) dom_full = dom_full && c;
+
+  // ---- grids and tiles ----
+  grids.clear();
+  tiles.clear();
+  sub_top.clear();
+  lp.assign(n + 1, LevelPlan());
+  std::vector<long long> gunk;  // unknowns per grid
+  auto add_tiles_for = [&](int gi) {
+    const GridDesc& g = grids[gi];
+    for (int y = 0; y <= g.ny; y += kTY)
+      for (int x = 0; x <= g.nx; x += kTX) tiles.push_back(Tile{gi, x, y});
+  };
+  auto unk_of = [&](int gi) {
+    while ((int)gunk.size() <= gi) gunk.push_back(-1);
+    if (gunk[gi] < 0) gunk[gi] = grid_unknowns(*this, grids[gi]);
+    return gunk[gi];
+  };
+  for (int L = 2; L <= n; ++L) {
+    LevelPlan& P = lp[L];
+    P.grid_begin = (int)grids.size();
+    long long pool = 0, pool64 = 0;
+    std::vector<std::vector<int>> sub_by_depth(L + 1), strip_by_depth(L - 1);
+    std::vector<int> sub_coarse, sub_topg, strip_coarse;
+    P.sub_top_off = (int)sub_top.size();
+    sub_top.resize(sub_top.size() + (size_t)B * m);
+    for (int b = 0; b < B; ++b) {
+      for (int j = 0; j < m; ++j) {
+        const auto& r = Om[j];
+        int job = b * m + j;
+        for (int dpt = 0; dpt <= L; ++dpt) {
+          int l = L - dpt;
+          GridDesc g{};
+          g.nx = (r[2] - r[0]) << l;
+          g.ny = (r[3] - r[1]) << l;
+          g.pitch = pitch_for(g.nx + 1);
+          g.ox = r[0] << l;
+          g.oy = r[1] << l;
+          g.level = l;
+          g.problem = b;
+          g.full = sub_full[j];
+          g.rshift = l;
+          g.rnx = r[2] - r[0];
+          g.rny = r[3] - r[1];
+          g.job = job;
+          g.depth = dpt;
+          g.roff = sub_roff[j];
+          g.off = pool;
+          pool += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
+          g.off64 = -1;
+          if (dpt == 0) {
+            g.off64 = pool64;
+            pool64 += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
+          }
+          int gi = (int)grids.size();
+          grids.push_back(g);
+          sub_by_depth[dpt].push_back(gi);
+          if (dpt == 0) {
+            sub_topg.push_back(gi);
+            sub_top[P.sub_top_off + job] = gi;
+          }
+          if (dpt == L) sub_coarse.push_back(gi);
+        }
+      }
+      for (int dpt = 0; dpt <= L - 2; ++dpt) {
+        int l = L - dpt;
+        GridDesc g{};
+        g.nx = ncx << l;
+        g.ny = ncy << l;
+        g.pitch = pitch_for(g.nx + 1);
+        g.ox = 0;
+        g.oy = 0;
+        g.level = l;
+        g.problem = b;
+        g.full = 0;
+        g.rshift = l - 2;
+        g.rnx = 4 * ncx;
+        g.rny = 4 * ncy;
+        g.job = B * m + b;
+        g.depth = dpt;
+        g.roff = strip_roff;
+        g.off = pool;
+        pool += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
+        g.off64 = -1;
+        if (dpt == 0) {
+          g.off64 = pool64;
+          pool64 += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
+        }
+        int gi = (int)grids.size();
+        grids.push_back(g);
+        strip_by_depth[dpt].push_back(gi);
+        if (dpt == L - 2) strip_coarse.push_back(gi);
+      }
+    }
+    P.grid_end = (int)grids.size();
+    P.sub.resize(L + 1);
+    for (int dpt = 0; dpt <= L; ++dpt) {
+      P.sub[dpt].off = (long long)tiles.size();
+      for (int gi : sub_by_depth[dpt]) {
+        add_tiles_for(gi);
+        P.sub[dpt].unk += unk_of(gi);
+      }
+      P.sub[dpt].count = (int)((long long)tiles.size() - P.sub[dpt].off);
+    }
+    P.strip.resize(L - 1);
+    for (int dpt = 0; dpt <= L - 2; ++dpt) {
+      P.strip[dpt].off = (long long)tiles.size();
+      for (int gi : strip_by_depth[dpt]) {
+        add_tiles_for(gi);
+        P.strip[dpt].unk += unk_of(gi);
+      }
+      P.strip[dpt].count = (int)((long long)tiles.size() - P.strip[dpt].off);
+    }
+    auto list_of = [&](const std::vector<int>& gl) {
+      TileList t;
+      t.off = (long long)tiles.size();
+      for (int gi : gl) {
+        tiles.push_back(Tile{gi, 0, 0});
+        t.unk += unk_of(gi);
+      }
+      t.count = (int)gl.size();
+      return t;
+    };
+    P.sub_coarsest = list_of(sub_coarse);
+    P.sub_top = list_of(sub_topg);
+    P.strip_coarsest = list_of(strip_coarse);
+    P.pool_elems = pool;
+    P.pool64_elems = pool64;
+    // unknown counts per problem (reports and the traffic model)
+    P.n_local = P.sub[0].unk / B;
+    P.n_strip = P.strip[0].unk / B;
+    {
+      long long nf = 0;
+      const int nxl = ncx << L, nyl = ncy << L;
+      for (int y = 1; y < nyl; ++y)
+        for (int x = 1; x < nxl; ++x) {
+          bool all = true;
+          for (int dy = -1; dy <= 0 && all; ++dy)
+            for (int dx = -1; dx <= 0 && all; ++dx) all = cell_in[((y + dy) >> L) * ncx + ((x + dx) >> L)] != 0;
+          nf += all;
+        }
+      P.n_free = nf;
+    }
+  }
+  // level-1 job grids (one job per problem), levels 1 .. l1_lc
+  l1_grid_begin = (int)grids.size();
+  l1_nlev = 1 - l1_lc + 1;
+  long long l1pool = 0;
+  for (int b = 0; b < B; ++b)
+    for (int dpt = 0; dpt < l1_nlev; ++dpt) {
+      int l = 1 - dpt;
+      GridDesc g{};
+      g.nx = lvl_nx(l);
+      g.ny = lvl_ny(l);
+      g.pitch = lvl_pitch(l);
+      g.level = l;
+      g.problem = b;
+      g.full = dom_full;
+      g.rshift = l - l1_lc;
+      g.rnx = lvl_nx(l1_lc);
+      g.rny = lvl_ny(l1_lc);
+      g.job = -1 - b;
+      g.depth = dpt;
+      g.roff = l1_roff;
+      g.off = l1pool;
+      l1pool += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
+      g.off64 = -1;
+      grids.push_back(g);
+    }
+  l1_pool_elems = l1pool;
+
+  // ---- workspace layout ----
+  size_t cur = 0;
+  auto take = [&](Span& s, size_t bytes) {
+    s.off = cur;
+    s.bytes = bytes;
+    cur += (bytes + 255) / 256 * 256;
+  };
+  take(w_grids, grids.size() * sizeof(GridDesc));
+  take(w_tiles, std::max<size_t>(1, tiles.size()) * sizeof(Tile));
+  take(w_regions, std::max<size_t>(16, regions.size()));
+  take(w_qlabel, qlabel.size() * sizeof(int16_t));
+  take(w_cellin, cell_in.size());
+  take(w_subtop, std::max<size_t>(1, sub_top.size()) * sizeof(int));
+  tables_bytes = cur;
+  // coefficient staging and per-level triangle values
+  size_t kst = 0;
+  if (kappa_kind == MLEV_KAPPA_PER_COARSE_CELL) kst = (size_t)B * ncx * ncy;
+  if (kappa_kind == MLEV_KAPPA_PER_FINE_ELEM) kst = (size_t)B * lvl_nx(n) * lvl_ny(n) * 2;
+  take(w_kstage, kst * 8);
+  std::memset(&kap_template, 0, sizeof(kap_template));
+  kap_template.kind = kappa_kind;
+  kap_template.ncx = ncx;
+  kap_template.ncy = ncy;
+  long long klv = 0;
+  for (int l = l1_lc; l <= n; ++l) {
+    bool need = (kappa_kind == MLEV_KAPPA_PER_FINE_ELEM) || (kappa_kind == MLEV_KAPPA_PER_COARSE_CELL && l < 0);
+    int i = l - MLEV_LMIN;
+    kap_template.lvl_off[i] = klv;
+    kap_template.lvl_bstride[i] = (long long)lvl_nx(l) * lvl_ny(l) * 2;
+    if (need) klv += (long long)B * lvl_nx(l) * lvl_ny(l) * 2;
+  }
+  take(w_klvl, (size_t)std::max<long long>(klv, 1) * 8);
+  take(w_band, (size_t)2 * B * nhb * (bw + 1) * 8);
+  const size_t gbytes = (size_t)B * glay.bstride * 8;
+  take(w_ut[0], gbytes);
+  take(w_ut[1], gbytes);
+  take(w_uin, gbytes);
+  take(w_r, gbytes);
+  const size_t l1bytes = (size_t)B * round_up((long long)(lvl_ny(1) + 1) * lvl_pitch(1), 64) * 8;
+  take(w_l1vec, 10 * l1bytes);
+  take(w_l1pool[0], (size_t)l1_pool_elems * tsize);
+  take(w_l1pool[1], (size_t)l1_pool_elems * tsize);
+  long long pmax = 0, p64max = 0;
+  for (int L = 2; L <= n; ++L) {
+    pmax = std::max(pmax, lp[L].pool_elems);
+    p64max = std::max(p64max, lp[L].pool64_elems);
+  }
+  take(w_x, (size_t)pmax * tsize);
+  take(w_f, (size_t)pmax * tsize);
+  take(w_x64, (size_t)p64max * 8);
+  take(w_aug, (size_t)B * ncx * ncy * 12 * 8);
+  take(w_lam, (size_t)B * (n + 1) * 8);
+  take(w_c, (size_t)B * (ncx + 1) * (ncy + 1) * 8);
+  take(w_c0, (size_t)B * 8);
+  take(w_stat, (size_t)B * mlev_stat_stride(n) * 8);
+  take(w_jobnorm, (size_t)B * (m + 1) * 2 * 8);
+  take(w_chol, (size_t)B * ((size_t)nhb * (bw + 1) + 4 * (size_t)nhb) * 8);
+  take(w_out_lam, (size_t)B * 8);
+  take(w_out_u, (size_t)B * (lvl_nx(n) + 1) * (lvl_ny(n) + 1) * 8);
+  ws_bytes = cur;
+  return "";
+}
+
+}  // namespace mlev

@@ -1,0 +1,97 @@
+// Host planner: validates the problem setup, derives the decomposition sets of
+// Section 4 (D_j, Omega_j, closed G_j, G_{m+1}) and lays out every device table and
+// buffer inside the caller's workspace.
+#pragma once
+
+#include <array>
+#include <string>
+#include <vector>
+
+#include "../../include/mlev.h"
+#include "mlev_internal.h"
+
+namespace mlev {
+
+struct TileList {
+  long long off = 0;   // first tile in the tile table
+  int count = 0;
+  long long unk = 0;   // unknown nodes of the grids covered (for the traffic model)
+};
+
+// Byte range of one workspace region.
+struct Span {
+  size_t off = 0;
+  size_t bytes = 0;
+};
+
+struct LevelPlan {                      // correction level L = k + 1
+  int grid_begin = 0, grid_end = 0;     // grids of this level in Plan::grids
+  std::vector<TileList> sub;            // node tiles of the depth-d grids of all subdomain jobs, d = 0..L
+  std::vector<TileList> strip;          // node tiles of the depth-d strip grids, d = 0..L-2
+  TileList sub_coarsest;                // one tile per subdomain job: (coarsest grid, 0, 0)
+  TileList strip_coarsest;
+  TileList sub_top;                     // one tile per subdomain job: (finest grid, 0, 0)
+  int sub_top_off = 0;                  // offset of this level's [B*m] table in Plan::sub_top
+  long long pool_elems = 0;             // X/F pool elements used
+  long long pool64_elems = 0;           // X64 pool elements used
+  long long n_local = 0, n_strip = 0;   // unknowns per problem
+  long long n_free = 0;                 // free nodes of the level-L lattice per problem
+};
+
+struct Plan {
+  // ---- inputs ----
+  int ncx = 0, ncy = 0;
+  double x0 = 0, y0 = 0, H = 0;
+  std::vector<uint8_t> cell_in;
+  int m = 0;
+  std::vector<int32_t> owner, overlap;
+  double delta = 0;
+  int glue_mode = 0;
+  int n = 0;
+  int B = 0;
+  int kappa_kind = 0;
+  std::vector<double> kappa_host;
+  const double* kappa_dev = nullptr;
+  bool kappa_on_device = false;
+  bool has_domain = false, has_partition = false, has_levels = false, has_forms = false;
+
+  // ---- derived ----
+  std::vector<std::array<int, 4>> D, Om;   // cell rectangles [x0, x1) x [y0, y1)
+  std::vector<std::array<int, 4>> G;       // closed G_j in quarter-lattice nodes [x0, x1] x [y0, y1]
+  std::vector<int16_t> qlabel;             // [4ncy][4ncx]
+  int l1_lc = 0;                           // coarsest level of the level-1 hierarchy (<= 0)
+  GlobalLayout glay{};
+  std::vector<GridDesc> grids;
+  std::vector<Tile> tiles;
+  std::vector<uint8_t> regions;
+  std::vector<int> sub_top;
+  std::vector<LevelPlan> lp;               // indexed by L, valid for 2..n
+  int l1_grid_begin = 0, l1_nlev = 0;      // level-1 job grids of problem b start at l1_grid_begin + b*l1_nlev
+  std::vector<TileList> l1_tiles;          // unused (level 1 runs in one block per problem)
+  long long l1_pool_elems = 0;
+  long long n_fine = 0;
+  int n_coarse = 0;
+  int nhb = 0, bw = 0;                     // coarse band system: rows (ncx-1)(ncy-1), half bandwidth
+
+  // ---- workspace layout (depends on opts) ----
+  int tsize = 4;
+  Span w_grids, w_tiles, w_regions, w_qlabel, w_cellin, w_subtop;
+  Span w_kstage, w_klvl, w_band, w_ut[2], w_uin, w_r, w_l1vec, w_l1pool[2];
+  Span w_x, w_f, w_x64, w_aug, w_lam, w_c, w_c0, w_stat, w_jobnorm, w_chol, w_out_lam, w_out_u;
+  size_t ws_bytes = 0;
+  size_t tables_bytes = 0;
+  KappaDev kap_template{};  // offsets relative to the workspace base
+
+  std::string build(const mlev_opts& o);   // "" on success, else a message
+  bool ready() const { return has_domain && has_partition && has_levels && has_forms; }
+
+  int lvl_nx(int l) const { return glay.nx[l - MLEV_LMIN]; }
+  int lvl_ny(int l) const { return glay.ny[l - MLEV_LMIN]; }
+  int lvl_pitch(int l) const { return glay.pitch[l - MLEV_LMIN]; }
+};
+
+// Validation helpers used by the C ABI (return "" if fine).
+std::string check_partition(Plan& p);
+long long grid_unknowns(const Plan& p, const GridDesc& g);
+
+}  // namespace mlev

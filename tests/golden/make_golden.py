@@ -1,0 +1,51 @@
+"""Write the oracle's results for the full-size workloads to tests/golden/*.json.
+
+Calls only the CPU oracle (oracle/) on the seeded inputs of workloads/; nothing here
+comes from the CUDA path. Each file holds lambda_{h_k} for k = 1..n and u_{h_n} sampled
+on a coarse sub-lattice (every `stride`-th node in x and y).
+
+Usage: python tests/golden/make_golden.py [name ...]
+"""
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+from oracle import multilevel as ML  # noqa: E402
+
+
+def record(p, members, stride):
+    out = {"problem": p.name, "levels": p.levels, "batch": p.batch, "stride": stride, "members": {}}
+    for b in members:
+        t = time.time()
+        r = ML.solve(p, b=b)
+        out["members"][str(b)] = {
+            "lam": r.lam,
+            "lam_levels": r.lam_levels,
+            "u_samples": r.u[::stride, ::stride].tolist(),
+            "oracle_seconds": time.time() - t,
+        }
+        print(p.name, b, r.lam, "%.1fs" % (time.time() - t), flush=True)
+    return out
+
+
+JOBS = {
+    "c2": lambda: record(W.config2(), [0], 64),
+    "c4": lambda: record(W.config4(), list(range(0, 256, 37)), 16),
+    "c5": lambda: record(W.config5(), [0], 32),
+    "c3n5": lambda: record(W.config3(levels=5), [0], 32),
+}
+
+if __name__ == "__main__":
+    names = sys.argv[1:] or list(JOBS)
+    for name in names:
+        data = JOBS[name]()
+        with open(os.path.join(HERE, f"oracle_{name}.json"), "w") as f:
+            json.dump(data, f)
