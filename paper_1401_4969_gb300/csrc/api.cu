@@ -28,8 +28,9 @@ struct mlev_ctx {
   long long uploaded_version = -1;
   long long version = 0;
   bool kappa_dirty = true;
-  // captured graph
+  // captured graph (captured on a private stream: the legacy default stream cannot capture)
   cudaGraphExec_t gexec = nullptr;
+  cudaStream_t capture_stream = nullptr;
   std::string graph_key;
   int launches = 0;
   int graph_launches = 0;
@@ -212,6 +213,7 @@ struct Launcher {
     double* klvl = at<double>(ws, P.w_klvl);
     G.kap.lvl = klvl;
     G.kap.coarse = P.kappa_kind == MLEV_KAPPA_PER_COARSE_CELL ? kappa_src : nullptr;
+    (void)cudaGetLastError();  // do not attribute an earlier unrelated failure to this solve
     long long* stat = at<long long>(ws, P.w_stat);
     const int stat_stride = mlev_stat_stride(n);
     cudaMemsetAsync(stat, 0, P.w_stat.bytes, s);
@@ -472,10 +474,14 @@ int solve_impl(mlev_ctx* ctx, const mlev_opts* o, void* ws, size_t ws_bytes, cud
         cudaGraphExecDestroy(ctx->gexec);
         ctx->gexec = nullptr;
       }
+      if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
       cudaGraph_t graph;
-      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      rc = o->precision == MLEV_PREC_FP64 ? ln.run<double>(lambda_out, u_out) : ln.run<float>(lambda_out, u_out);
-      cudaError_t e = cudaStreamEndCapture(s, &graph);
+      Launcher cap{ctx, P, *o, ws, ctx->capture_stream};
+      cap.kappa_src = kappa_src;
+      CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+      rc = o->precision == MLEV_PREC_FP64 ? cap.run<double>(lambda_out, u_out) : cap.run<float>(lambda_out, u_out);
+      cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+      ln.count = cap.count;
       if (rc) return rc;
       if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
       e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
@@ -548,6 +554,7 @@ int mlev_create(mlev_ctx** out, int device) {
 void mlev_destroy(mlev_ctx* ctx) {
   if (!ctx) return;
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
 }
