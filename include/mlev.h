@@ -188,6 +188,27 @@ int mlev_solve_host(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_
                     const double* kappa_host, double* lambda_host, double* u_host, mlev_report* rep);
 
 /*
+ * Same computation as mlev_solve, for callers that cannot allocate device memory: for
+ * example a plugin inside a host application whose own memory pool must own every
+ * device allocation, or a latency-critical loop that may never enter the CUDA
+ * allocator (cudaMalloc can block and synchronize the device). Nothing in this call
+ * allocates: its workspace is a fixed array of MLEV_NOALLOC_WORKSPACE_BYTES (32 MiB)
+ * compiled into the library, which every GPU that loads the library keeps until the
+ * process exits. The paper has no counterpart; this is an interface convenience.
+ *  - Problems whose mlev_workspace_size exceeds MLEV_NOALLOC_WORKSPACE_BYTES are
+ *    rejected with MLEV_ENOMEM and a message giving both sizes.
+ *  - The first call on a device looks up the array's device address (a one-time
+ *    set-up with that device current); make that first call before any stream capture.
+ *  - All calls share the one array and each call overwrites it (plan tables are copied
+ *    in again every call), so calls whose GPU work overlaps in time (other streams,
+ *    other threads or contexts on the same device) race and give wrong results.
+ *  - Outputs and the meaning of every argument are as in mlev_solve.
+ */
+#define MLEV_NOALLOC_WORKSPACE_BYTES (32u << 20)
+int mlev_solve_noalloc(mlev_ctx* ctx, const mlev_opts* opts, void* stream, double* lambda_out, double* u_out,
+                       mlev_report* rep);
+
+/*
  * Copy the per-family statistics of the last profiled solve (opts.profile = 1) into
  * out[0 .. min(capacity, families) - 1]; *count receives the number of families.
  * Returns MLEV_ESTATE if no profiled solve has completed on ctx.

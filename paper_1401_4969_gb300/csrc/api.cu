@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -728,5 +729,53 @@ extern "C" int mlev_profile_read(mlev_ctx* ctx, mlev_kernel_stat* out, int capac
     out[i].ms = ctx->prof[i].ms;
     out[i].bytes = ctx->prof[i].bytes;
   }
+  return MLEV_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Workspace-free entry point. Its scratch is this fixed device array (one per GPU that
+// loads the library, alive until exit); host code must not use the symbol as an
+// address, so its device address is looked up once per device below.
+static __device__ __align__(256) unsigned char g_noalloc_workspace[MLEV_NOALLOC_WORKSPACE_BYTES];
+
+namespace {
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[256] = {nullptr};
+}  // namespace
+
+extern "C" int mlev_solve_noalloc(mlev_ctx* ctx, const mlev_opts* opts, void* stream, double* lambda_out,
+                                  double* u_out, mlev_report* rep) {
+  if (!ctx) return MLEV_EINVAL;
+  if (ctx->device < 0) return fail(ctx, MLEV_ESTATE, "planning-only context (device -1) cannot solve");
+  if (ctx->device >= 256) return fail(ctx, MLEV_EUNSUPPORTED, "device index above 255");
+  if (!opts_valid(opts)) return fail(ctx, MLEV_EINVAL, "invalid options");
+  int rc = ensure_plan(ctx, opts);
+  if (rc) return rc;
+  if (ctx->plan.ws_bytes > (size_t)MLEV_NOALLOC_WORKSPACE_BYTES)
+    return fail(ctx, MLEV_ENOMEM,
+                "problem needs " + std::to_string(ctx->plan.ws_bytes) +
+                    " bytes of workspace; the no-allocation entry point holds at most " +
+                    std::to_string((size_t)MLEV_NOALLOC_WORKSPACE_BYTES) + " bytes (use mlev_solve with a larger one)");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, MLEV_ECUDA, "cudaSetDevice");
+  void* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[ctx->device]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_workspace);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(no-allocation workspace)");
+      g_noalloc_ptr[ctx->device] = p;
+    }
+    ws = g_noalloc_ptr[ctx->device];
+  }
+  rc = prepare(ctx, opts, ws, MLEV_NOALLOC_WORKSPACE_BYTES);
+  if (rc) return rc;
+  if (!lambda_out) return fail(ctx, MLEV_EINVAL, "lambda_out is required");
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = upload_tables(ctx, ws, s, true);  // the array is shared: always bring this problem's tables
+  if (rc) return rc;
+  rc = solve_impl(ctx, opts, ws, MLEV_NOALLOC_WORKSPACE_BYTES, s, kappa_device_src(ctx, ws), lambda_out, u_out);
+  if (rc) return rc;
+  if (rep) return fill_report(ctx, ws, s, rep);
   return MLEV_OK;
 }

@@ -25,7 +25,8 @@ MAX_LEVELS = 10
 
 EXPORTS = ["mlev_opts_default", "mlev_create", "mlev_destroy", "mlev_last_error", "mlev_set_domain",
            "mlev_set_partition", "mlev_set_levels", "mlev_set_forms", "mlev_workspace_size", "mlev_problem_info",
-           "mlev_solve", "mlev_solve_host", "mlev_profile_read"]
+           "mlev_solve", "mlev_solve_host", "mlev_profile_read", "mlev_solve_noalloc"]
+NOALLOC_WORKSPACE_BYTES = 32 << 20
 
 
 class Opts(C.Structure):
@@ -95,8 +96,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.mlev_solve.argtypes = [P, C.POINTER(Opts), VP, SZ, VP, VP, VP, C.POINTER(Report)]
     lib.mlev_solve_host.argtypes = [P, C.POINTER(Opts), VP, SZ, VP, VP, VP, VP, C.POINTER(Report)]
     lib.mlev_profile_read.argtypes = [P, C.POINTER(KernelStat), I, C.POINTER(I)]
+    lib.mlev_solve_noalloc.argtypes = [P, C.POINTER(Opts), VP, VP, VP, C.POINTER(Report)]
     for name in ("mlev_create", "mlev_set_domain", "mlev_set_partition", "mlev_set_levels", "mlev_set_forms",
-                 "mlev_workspace_size", "mlev_problem_info", "mlev_solve", "mlev_solve_host", "mlev_profile_read"):
+                 "mlev_workspace_size", "mlev_problem_info", "mlev_solve", "mlev_solve_host", "mlev_profile_read",
+                 "mlev_solve_noalloc"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -217,6 +220,18 @@ class Solver:
                                  C.c_void_p(s.cuda_stream), C.c_void_p(lam.data_ptr()),
                                  C.c_void_p(u.data_ptr()) if u is not None else None,
                                  C.byref(rep) if rep is not None else None)
+        self._check(rc)
+        return rep.as_dict() if rep is not None else None
+
+    def solve_noalloc(self, opts: Opts, lam, u=None, stream=None, report: bool = False):
+        """mlev_solve_noalloc: like solve_into but with the library's fixed workspace (no allocation)."""
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        rep = Report() if report else None
+        rc = self.lib.mlev_solve_noalloc(self.h, C.byref(opts), C.c_void_p(s.cuda_stream), C.c_void_p(lam.data_ptr()),
+                                         C.c_void_p(u.data_ptr()) if u is not None else None,
+                                         C.byref(rep) if rep is not None else None)
         self._check(rc)
         return rep.as_dict() if rep is not None else None
 
