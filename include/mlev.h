@@ -74,7 +74,8 @@ typedef struct mlev_opts {
   double omega;         /* over-relaxation of the red-black Gauss-Seidel smoother (1 = plain GS) */
   int check_residuals;  /* 1: measure the final relative residual of every local / G_{m+1} solve */
   int profile;          /* 1: time every launch with CUDA events (no graph); read with mlev_profile_read */
-  int reserved[4];
+  int fused;            /* 1: fused multigrid kernels (down / up / shared-memory tail); 0: one launch per operation */
+  int reserved[3];
 } mlev_opts;
 
 /* Per-solve diagnostics (batch member 0 unless noted). */

@@ -78,9 +78,9 @@ bool opts_valid(const mlev_opts* o) {
 
 std::string opts_key(const mlev_opts* o) {
   char b[256];
-  snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%.17g/%d/%.17g/%d", o->precision, o->vcycles, o->refine_passes,
-           o->strip_vcycles, o->pre_smooth, o->post_smooth, o->coarse_sweeps, o->level1_max_iter, o->level1_tol,
-           o->rr_max_iter, o->omega, o->check_residuals);
+  snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%.17g/%d/%.17g/%d/%d", o->precision, o->vcycles,
+           o->refine_passes, o->strip_vcycles, o->pre_smooth, o->post_smooth, o->coarse_sweeps, o->level1_max_iter,
+           o->level1_tol, o->rr_max_iter, o->omega, o->check_residuals, o->fused);
   return b;
 }
 
@@ -92,12 +92,13 @@ P* at(void* base, const Span& s) {
 // Kernel families for profiling (names reported by mlev_profile_read).
 enum Fam {
   F_KAPPA, F_BAND, F_LEVEL1, F_INTERP, F_RHS, F_GATHER, F_SMOOTH, F_RESTRICT, F_PROLONG, F_COARSEST, F_ACCUM,
-  F_REFINE, F_GLUE, F_STRIP_RHS, F_STRIP_UPD, F_AUG, F_RR, F_OUT, F_RESNORM, F_COUNT
+  F_REFINE, F_GLUE, F_STRIP_RHS, F_STRIP_UPD, F_AUG, F_RR, F_OUT, F_RESNORM, F_MG_DOWN, F_MG_UP, F_MG_TAIL, F_COUNT
 };
 const char* kFamName[F_COUNT] = {"kappa_levels", "coarse_band", "level1_lobpcg", "interp_embed", "rhs_aux",
                                  "mg_gather", "mg_smooth", "mg_restrict", "mg_prolong", "mg_coarsest",
                                  "mixed_accumulate", "mixed_refine_residual", "glue", "strip_rhs", "strip_update",
-                                 "aug_inner", "rayleigh_ritz", "output", "residual_check"};
+                                 "aug_inner", "rayleigh_ritz", "output", "residual_check", "mg_down_fused",
+                                 "mg_up_fused", "mg_tail"};
 
 struct ProfRec {
   int fam;
@@ -148,8 +149,29 @@ struct Launcher {
   // Traffic model, bytes per unknown (t = bytes of T): see the design notes.
   double kfine_extra() const { return P.kappa_kind == MLEV_KAPPA_PER_FINE_ELEM ? 48.0 : 0.0; }
 
+  // how the coarsest grid of a job set is solved
+  enum Coarse { C_SWEEPS = 0, C_DIRECT = 1, C_SMEM = 2 };
+
   template <typename T>
-  void vcycle(const std::vector<TileList>& lists, const TileList& coarsest, T* X, T* F) {
+  void coarse_solve(int mode, const TileList& coarsest, T* X, T* F) {
+    const double t = sizeof(T);
+    if (mode == C_DIRECT) {
+      T* inv = at<T>(ws, P.w_cinv);
+      go(F_COARSEST, t * (double)coarsest.count * P.nd_max * P.nd_max,
+         [&] { launch_coarsest_direct<T>(G, tiles_at(coarsest), coarsest.count, X, F, inv, P.nd_max, s); });
+    } else if (mode == C_SMEM) {
+      go(F_COARSEST, 4 * t * coarsest.unk, [&] {
+        launch_coarsest_smem<T>(G, tiles_at(coarsest), coarsest.count, P.strip_coarse_nodes, X, F, o.coarse_sweeps,
+                                o.omega, s);
+      });
+    } else {
+      go(F_COARSEST, 4 * t * coarsest.unk * o.coarse_sweeps,
+         [&] { launch_coarsest<T>(G, tiles_at(coarsest), coarsest.count, X, F, o.coarse_sweeps, o.omega, s); });
+    }
+  }
+
+  template <typename T>
+  void vcycle(const std::vector<TileList>& lists, const TileList& coarsest, T* X, T* F, int cmode) {
     const double t = sizeof(T);
     const int D = (int)lists.size() - 1;
     auto smooth = [&](int d, int color) {
@@ -164,8 +186,7 @@ struct Launcher {
       go(F_RESTRICT, (10 * t + 4 * kfine_extra()) * lists[d + 1].unk,
          [&] { launch_restrict<T>(G, tiles_at(lists[d + 1]), lists[d + 1].count, X, F, s); });
     }
-    go(F_COARSEST, 4 * t * coarsest.unk * o.coarse_sweeps,
-       [&] { launch_coarsest<T>(G, tiles_at(coarsest), coarsest.count, X, F, o.coarse_sweeps, o.omega, s); });
+    coarse_solve<T>(cmode, coarsest, X, F);
     for (int d = D - 1; d >= 0; --d) {
       go(F_PROLONG, 2.25 * t * lists[d].unk, [&] { launch_prolong<T>(G, tiles_at(lists[d]), lists[d].count, X, s); });
       for (int k = 0; k < o.post_smooth; ++k) {
@@ -175,10 +196,44 @@ struct Launcher {
     }
   }
 
+  // One V-cycle with the fused kernels: down (smooth + restrict) on the depths above the
+  // tail, the tail (rest of the cycle in shared memory, one block per job), then up.
+  template <typename T>
+  void vcycle_fused(const std::vector<TileList>& fl, int dt, int D, const TileList& tail, size_t tail_smem, T* X, T* F,
+                    bool direct) {
+    const double t = sizeof(T);
+    for (int d = 0; d < dt; ++d)
+      go(F_MG_DOWN, (3.5 * t + o.pre_smooth * kfine_extra()) * fl[d].unk,
+         [&] { launch_mg_down<T>(G, tiles_at(fl[d]), fl[d].count, X, F, o.pre_smooth, o.omega, s); });
+    const T* inv = direct ? at<T>(ws, P.w_cinv) : nullptr;
+    if (dt == D && !direct &&
+        coarsest_smem_bytes(P.kappa_kind, P.strip_coarse_nodes, sizeof(T)) <= 220 * 1024) {
+      // the tail is the coarsest grid alone: staged sweeps with precomputed coefficients
+      go(F_COARSEST, 4 * t * tail.unk, [&] {
+        launch_coarsest_smem<T>(G, tiles_at(tail), tail.count, P.strip_coarse_nodes, X, F, o.coarse_sweeps, o.omega,
+                                s);
+      });
+    } else {
+      go(F_MG_TAIL, 3.0 * t * tail.unk, [&] {
+        // nd_max sizes the dense-solve buffer, which only direct (subdomain) tails have: it
+        // must match the planner's shared-memory size
+        launch_mg_tail<T>(G, tiles_at(tail), tail.count, X, F, inv, direct ? P.nd_max : 0, D - dt + 1,
+                          o.pre_smooth, o.post_smooth, o.coarse_sweeps, o.omega, dt == 0 ? 1 : 0, tail_smem, s);
+      });
+    }
+    for (int d = dt - 1; d >= 0; --d)
+      go(F_MG_UP, (3.25 * t + o.post_smooth * kfine_extra()) * fl[d].unk,
+         [&] { launch_mg_up<T>(G, tiles_at(fl[d]), fl[d].count, X, F, o.post_smooth, o.omega, s); });
+  }
+
   // passes of V-cycles with FP64 residual refinement in between (mixed) on one job set
   template <typename T>
   void solve_set(const std::vector<TileList>& lists, const TileList& coarsest, int vcycles, T* X, T* F, double* X64,
-                 const double* R) {
+                 const double* R, int cmode, const std::vector<TileList>* fl = nullptr, int dt = 0,
+                 const TileList* tail = nullptr, size_t tail_smem = 0) {
+    const int D = (int)lists.size() - 1;
+    const bool fused = o.fused && fl && tail && dt <= D && o.pre_smooth >= 1 && o.pre_smooth <= 2 &&
+                       o.post_smooth >= 1 && o.post_smooth <= 2;
     const bool mixed = sizeof(T) == 4;
     const double t = sizeof(T);
     const int passes = mixed ? o.refine_passes : 1;
@@ -190,7 +245,12 @@ struct Launcher {
         go(F_REFINE, (16 + t + kfine_extra()) * top.unk,
            [&] { launch_refine_residual<T>(G, P.glay, tiles_at(top), top.count, F, X64, R, s); });
       }
-      for (int v = 0; v < cyc; ++v) vcycle<T>(lists, coarsest, X, F);
+      for (int v = 0; v < cyc; ++v) {
+        if (fused)
+          vcycle_fused<T>(*fl, dt, D, *tail, tail_smem, X, F, cmode == C_DIRECT);
+        else
+          vcycle<T>(lists, coarsest, X, F, cmode);
+      }
     }
     if (mixed)
       go(F_ACCUM, (2 * t + 16) * top.unk, [&] { launch_accumulate<T>(G, tiles_at(top), top.count, X, X64, s); });
@@ -233,6 +293,17 @@ struct Launcher {
     double* KH = at<double>(ws, P.w_band);
     double* MH = KH + (size_t)B * P.nhb * (P.bw + 1);
     go(F_BAND, 16.0 * B * P.nhb * (P.bw + 1), [&] { launch_band_setup(G, B, P.nhb, P.bw, KH, MH, s); });
+    // coarsest-grid solvers: dense inverses of the subdomain T_H windows (shared by every
+    // correction level), staged sweeps for the strip when its T_{h_2} grid fits on chip
+    const int sub_cmode = P.sub_direct ? C_DIRECT : C_SWEEPS;
+    const int strip_cmode =
+        coarsest_smem_bytes(P.kappa_kind, P.strip_coarse_nodes, sizeof(T)) <= 220 * 1024 ? C_SMEM : C_SWEEPS;
+    if (P.sub_direct) {
+      const TileList& cl = P.lp[n].sub_coarsest;
+      T* inv = at<T>(ws, P.w_cinv);
+      go(F_COARSEST, 8.0 * cl.count * P.nd_max * P.nd_max,
+         [&] { launch_coarse_inverse<T>(G, tiles_at(cl), cl.count, inv, P.nd_max, s); });
+    }
     double* ut[2] = {at<double>(ws, P.w_ut[0]), at<double>(ws, P.w_ut[1])};
     double* uin = at<double>(ws, P.w_uin);
     double* r = at<double>(ws, P.w_r);
@@ -251,7 +322,7 @@ struct Launcher {
       a.fpool = at<void>(ws, P.w_l1pool[1]);
       a.pre = o.pre_smooth;
       a.post = o.post_smooth;
-      a.coarse_sweeps = o.coarse_sweeps;
+      a.coarse_sweeps = std::max(4, o.coarse_sweeps / 4);  // level-1 coarsest grid: a few nodes
       a.omega = o.omega;
       a.max_iter = o.level1_max_iter;
       a.tol = o.level1_tol;
@@ -286,11 +357,15 @@ struct Launcher {
       a.lam_stride = n + 1;
       go(F_INTERP, 10.0 * nfree, [&] { launch_interp(G, P.glay, a, s); });
       go(F_RHS, (16.0 + kfine_extra()) * nfree, [&] { launch_rhs(G, P.glay, a, s); });
+      // multigrid pools of this level start at zero: nodes that are not unknowns must read
+      // as 0 (the fused kernels skip tiles without unknowns)
+      cudaMemsetAsync(X, 0, (size_t)lp.pool_elems * sizeof(T), s);
       // step 1: auxiliary problems on every Omega_j of every batch member
       const TileList& top = lp.sub[0];
       go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * top.unk,
          [&] { launch_gather<T>(G, P.glay, tiles_at(top), top.count, X, F, X64, r, s); });
-      solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, r);
+      solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, r, sub_cmode, &lp.sub_f, lp.sub_dt, &lp.sub_tail,
+                   lp.sub_tail_smem);
       const double* E = mixed ? X64 : reinterpret_cast<const double*>(X);
       if (o.check_residuals) {
         cudaMemsetAsync(jobnorm, 0, P.w_jobnorm.bytes, s);
@@ -305,7 +380,8 @@ struct Launcher {
       if (stop.count) {
         go(F_STRIP_RHS, (32.0 + 2 * t + kfine_extra()) * stop.unk,
            [&] { launch_strip_rhs<T>(G, P.glay, a, tiles_at(stop), stop.count, X, F, X64, s); });
-        solve_set<T>(lp.strip, lp.strip_coarsest, o.strip_vcycles, X, F, X64, r);
+        solve_set<T>(lp.strip, lp.strip_coarsest, o.strip_vcycles, X, F, X64, r, strip_cmode, &lp.strip_f,
+                     lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem);
         if (o.check_residuals) {
           cudaMemsetAsync(jobnorm, 0, P.w_jobnorm.bytes, s);
           go(F_RESNORM, 16.0 * stop.unk,
@@ -334,6 +410,7 @@ struct Launcher {
       rr.stat = stat;
       rr.stat_stride = stat_stride;
       rr.max_iter = o.rr_max_iter;
+      rr.smem = rr_smem_bytes(P.nhb, P.bw) <= (size_t)kRRSmemMax;
       go(F_RR, 0.0, [&] { launch_rr(G, rr, s); });
     }
     go(F_OUT, 16.0 * B, [&] { launch_lambda_out(B, n, lam, lambda_out, s); });
@@ -527,6 +604,7 @@ void mlev_opts_default(mlev_opts* o) {
   o->use_graph = 0;
   o->omega = 1.0;
   o->check_residuals = 0;
+  o->fused = 1;
 }
 
 int mlev_create(mlev_ctx** out, int device) {

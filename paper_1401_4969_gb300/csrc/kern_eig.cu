@@ -16,90 +16,10 @@
 //   unique root; it is found by Newton's method safeguarded by bisection, with a
 //   banded Cholesky factorisation of S(mu) per step. The eigenvector is
 //   c = [-S(mu)^{-1} w ; 1], scaled to b(u,u) = 1 and int u > 0.
+#include "kern_blk.cuh"
 #include "kern_launch.h"
 
 namespace mlev {
-
-// ---------------------------------------------------------------- in-block multigrid
-template <typename T, int KK>
-__device__ void blk_smooth(const DevGeom& G, const GridDesc& g, T* X, const T* F, int sweeps, bool reverse, T omega) {
-  const int nn = (g.nx + 1) * (g.ny + 1);
-  T* x = X + g.off;
-  for (int s = 0; s < sweeps; ++s)
-    for (int cc = 0; cc < 2; ++cc) {
-      const int color = reverse ? 1 - cc : cc;
-      for (int q = threadIdx.x; q < nn; q += blockDim.x) {
-        const int i = q % (g.nx + 1), j = q / (g.nx + 1);
-        if (((i + j) & 1) != color || !is_unknown(G, g, i, j)) continue;
-        const long long c = (long long)j * g.pitch + i;
-        const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
-        const T v = F[g.off + c] + (T)w.e * x[c + 1] + (T)w.w * x[c - 1] + (T)w.n * x[c + g.pitch] +
-                    (T)w.s * x[c - g.pitch];
-        x[c] += omega * (v / (T)(w.e + w.w + w.n + w.s) - x[c]);
-      }
-      __syncthreads();
-    }
-}
-
-template <typename T, int KK>
-__device__ __forceinline__ T blk_res(const DevGeom& G, const GridDesc& g, const T* X, const T* F, int i, int j) {
-  if (!is_unknown(G, g, i, j)) return (T)0;
-  const long long c = (long long)j * g.pitch + i;
-  const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
-  return F[g.off + c] - apply_k<T, T>(X + g.off, c, g.pitch, w);
-}
-
-template <typename T, int KK>
-__device__ void blk_restrict(const DevGeom& G, const GridDesc& gf, const GridDesc& gc, T* X, T* F) {
-  const int nn = (gc.nx + 1) * (gc.ny + 1);
-  for (int q = threadIdx.x; q < nn; q += blockDim.x) {
-    const int I = q % (gc.nx + 1), J = q / (gc.nx + 1);
-    const long long cc = (long long)J * gc.pitch + I;
-    X[gc.off + cc] = (T)0;
-    if (!is_unknown(G, gc, I, J)) continue;
-    const int i = 2 * I, j = 2 * J;
-    const T half = blk_res<T, KK>(G, gf, X, F, i + 1, j) + blk_res<T, KK>(G, gf, X, F, i - 1, j) +
-                   blk_res<T, KK>(G, gf, X, F, i, j + 1) + blk_res<T, KK>(G, gf, X, F, i, j - 1) +
-                   blk_res<T, KK>(G, gf, X, F, i + 1, j + 1) + blk_res<T, KK>(G, gf, X, F, i - 1, j - 1);
-    F[gc.off + cc] = blk_res<T, KK>(G, gf, X, F, i, j) + (T)0.5 * half;
-  }
-  __syncthreads();
-}
-
-template <typename T>
-__device__ void blk_prolong(const DevGeom& G, const GridDesc& gf, const GridDesc& gc, T* X) {
-  const int nn = (gf.nx + 1) * (gf.ny + 1);
-  const T* xc = X + gc.off;
-  for (int q = threadIdx.x; q < nn; q += blockDim.x) {
-    const int i = q % (gf.nx + 1), j = q / (gf.nx + 1);
-    if (!is_unknown(G, gf, i, j)) continue;
-    const int I = i >> 1, J = j >> 1;
-    T v;
-    if (!(i & 1) && !(j & 1))
-      v = xc[(long long)J * gc.pitch + I];
-    else if ((i & 1) && !(j & 1))
-      v = (T)0.5 * (xc[(long long)J * gc.pitch + I] + xc[(long long)J * gc.pitch + I + 1]);
-    else if (!(i & 1) && (j & 1))
-      v = (T)0.5 * (xc[(long long)J * gc.pitch + I] + xc[(long long)(J + 1) * gc.pitch + I]);
-    else
-      v = (T)0.5 * (xc[(long long)J * gc.pitch + I] + xc[(long long)(J + 1) * gc.pitch + I + 1]);
-    X[gf.off + (long long)j * gf.pitch + i] += v;
-  }
-  __syncthreads();
-}
-
-template <typename T, int KK>
-__device__ void blk_vcycle(const DevGeom& G, int g0, int nlev, T* X, T* F, int pre, int post, int csweeps, T omega) {
-  for (int d = 0; d + 1 < nlev; ++d) {
-    blk_smooth<T, KK>(G, G.grids[g0 + d], X, F, pre, false, omega);
-    blk_restrict<T, KK>(G, G.grids[g0 + d], G.grids[g0 + d + 1], X, F);
-  }
-  blk_smooth<T, KK>(G, G.grids[g0 + nlev - 1], X, F, csweeps, false, omega);
-  for (int d = nlev - 2; d >= 0; --d) {
-    blk_prolong<T>(G, G.grids[g0 + d], G.grids[g0 + d + 1], X);
-    blk_smooth<T, KK>(G, G.grids[g0 + d], X, F, post, true, omega);
-  }
-}
 
 // ---------------------------------------------------------------- small dense helpers
 // Smallest eigenpair of the symmetric-definite pencil (A, B) of order n <= 3 with
@@ -262,7 +182,7 @@ __global__ void __launch_bounds__(1024) k_level1(DevGeom G, GlobalLayout gl, Lev
       xp[g.off + c] = (T)0;
     }
     __syncthreads();
-    blk_vcycle<T, KK>(G, g0, a.nlev, xp, fp, a.pre, a.post, a.coarse_sweeps, (T)a.omega);
+    blk_vcycle<T, KK>(G, G.grids + g0, a.nlev, xp, fp, a.pre, a.post, a.coarse_sweeps, (T)a.omega, nullptr);
     for (int q = threadIdx.x; q < nn; q += blockDim.x) {
       const long long c = (long long)(q / (nx + 1)) * pitch + q % (nx + 1);
       W[c] = (double)xp[g.off + c];
@@ -366,58 +286,52 @@ template void launch_level1<float>(const DevGeom&, const GlobalLayout&, const Le
 template void launch_level1<double>(const DevGeom&, const GlobalLayout&, const Level1Args&, cudaStream_t);
 
 // ---------------------------------------------------------------- Rayleigh-Ritz
-// Band Cholesky of S = K - mu M in place (row-major band [r][d] = S(r, r-d)).
-// Returns false (to all threads) if a pivot is not positive.
-__device__ bool band_chol(double* Lb, int N, int bw, int* flag) {
+// Band LDL^T factorisation of S = K_H - mu M_H (row-major band [r][d] = S(r, r-d)) with
+// the right-hand side eliminated alongside (forward substitution of L z = w), one block
+// barrier per column. On return Lb holds the unscaled columns (L(i,j) = Lb[i][i-j] / D_j),
+// invD[j] = 1 / D_j and y = z. Returns false (to all threads) if a pivot is not positive,
+// i.e. mu is not below the smallest eigenvalue of (K_H, M_H).
+__device__ bool band_ldlt(double* Lb, double* invD, double* y, const int* pairs, int npair, int N, int bw,
+                          int* flag) {
+  const int bw1 = bw + 1;
   if (threadIdx.x == 0) *flag = 1;
   __syncthreads();
-  __shared__ double inv;
-  const int bw1 = bw + 1;
-  const int npair = bw * (bw + 1) / 2;
   for (int j = 0; j < N; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = Lb[(long long)j * bw1];
-      if (!(d > 0.0)) *flag = 0;
-      const double sd = sqrt(fmax(d, 1e-300));
-      Lb[(long long)j * bw1] = sd;
-      inv = 1.0 / sd;
+    const double Dj = Lb[(long long)j * bw1];
+    if (!(Dj > 0.0)) {  // identical decision in every thread
+      if (threadIdx.x == 0) *flag = 0;
+      return false;
     }
-    __syncthreads();
-    if (!*flag) return false;
+    const double inv = 1.0 / Dj;
     const int last = min(N - 1, j + bw);
-    for (int t = threadIdx.x; t < last - j; t += blockDim.x) Lb[(long long)(j + 1 + t) * bw1 + t + 1] *= inv;
-    __syncthreads();
-    for (int q = threadIdx.x; q < npair; q += blockDim.x) {
-      // pair (a, b), 0 <= b <= a < bw  ->  rows i = j+1+a, k = j+1+b
-      int aa = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
-      while ((aa + 1) * (aa + 2) / 2 <= q) ++aa;
-      while (aa * (aa + 1) / 2 > q) --aa;
-      const int bb = q - aa * (aa + 1) / 2;
-      const int i = j + 1 + aa, k = j + 1 + bb;
-      if (i > last) continue;
-      Lb[(long long)i * bw1 + (i - k)] -= Lb[(long long)i * bw1 + (i - j)] * Lb[(long long)k * bw1 + (k - j)];
+    const double yj = y[j];
+    for (int q = threadIdx.x; q < npair + bw; q += blockDim.x) {
+      if (q < npair) {
+        const int aa = pairs[q] >> 16, bb = pairs[q] & 0xffff;
+        const int i = j + 1 + aa, k = j + 1 + bb;
+        if (i <= last)
+          Lb[(long long)i * bw1 + (i - k)] -= Lb[(long long)i * bw1 + (i - j)] * Lb[(long long)k * bw1 + (k - j)] * inv;
+      } else {
+        const int i = j + 1 + (q - npair);
+        if (i <= last) y[i] -= Lb[(long long)i * bw1 + (i - j)] * inv * yj;
+      }
     }
+    if (threadIdx.x == 0) invD[j] = inv;
     __syncthreads();
   }
   return true;
 }
 
-// Solve L L^T x = rhs (band factor) with warp 0; x may alias rhs.
-__device__ void band_solve(const double* Lb, int N, int bw, const double* rhs, double* x) {
+// Back substitution L^T x = D^{-1} z in place (x overwrites y), warp 0, column-oriented.
+__device__ void band_back(const double* Lb, const double* invD, double* y, int N, int bw) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x, bw1 = bw + 1;
-    for (int i = 0; i < N; ++i) {
-      double s = 0.0;
-      for (int d = 1 + lane; d <= min(bw, i); d += 32) s += Lb[(long long)i * bw1 + d] * x[i - d];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = (rhs[i] - s) / Lb[(long long)i * bw1];
-      __syncwarp();
-    }
     for (int i = N - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int d = 1 + lane; d <= min(bw, N - 1 - i); d += 32) s += Lb[(long long)(i + d) * bw1 + d] * x[i + d];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] = (x[i] - s) / Lb[(long long)i * bw1];
+      const double xi = y[i] * invD[i];
+      __syncwarp();
+      if (lane == 0) y[i] = xi;
+      // remove x_i from the rows above it: z[i-d] -= L(i, i-d) D_{i-d} x_i = Lb[i][d] x_i
+      for (int d = 1 + lane; d <= bw && i - d >= 0; d += 32) y[i - d] -= Lb[(long long)i * bw1 + d] * xi;
       __syncwarp();
     }
   }
@@ -425,21 +339,30 @@ __device__ void band_solve(const double* Lb, int N, int bw, const double* rhs, d
 }
 
 __global__ void __launch_bounds__(256) k_rr(DevGeom G, RRArgs a) {
+  extern __shared__ double rr_sm[];
   __shared__ double scratch[8 * 4];
   __shared__ double red[4];
   __shared__ int flag;
-  __shared__ double sh_mu;
-  __shared__ int sh_done;
   const int p = blockIdx.x, N = a.nhb, bw = a.bw, bw1 = bw + 1;
   const int ncx = G.ncx, ncy = G.ncy;
-  double* Lb = a.chol + (long long)p * ((long long)N * bw1 + 4LL * N);
+  const int npair = bw * (bw + 1) / 2;
+  // band + vectors in shared memory when they fit (a.smem), else in the global scratch
+  double* base = a.smem ? rr_sm : a.chol + (long long)p * ((long long)N * bw1 + 5LL * N);
+  double* Lb = base;
   double* ga = Lb + (long long)N * bw1;
   double* gb = ga + N;
   double* wv = gb + N;
   double* y = wv + N;
+  double* invD = y + N;
+  int* pairs = reinterpret_cast<int*>(a.smem ? invD + N : rr_sm);
   const double* KH = a.KH + (long long)p * N * bw1;
   const double* MH = a.MH + (long long)p * N * bw1;
   const double* part = a.partials + (long long)p * ncx * ncy * 12;
+  for (int q = threadIdx.x; q < npair; q += blockDim.x) {
+    int aa = 0;
+    while ((aa + 1) * (aa + 2) / 2 <= q) ++aa;
+    pairs[q] = (aa << 16) | (q - aa * (aa + 1) / 2);
+  }
   // ---- reduce the per-cell partials: alpha, beta, sigma, g_a, g_b
   {
     double v[3] = {0.0, 0.0, 0.0};
@@ -468,86 +391,77 @@ __global__ void __launch_bounds__(256) k_rr(DevGeom G, RRArgs a) {
   }
   __syncthreads();
 
-  // f(mu) and f'(mu) given a successful factorisation at mu: y = S^{-1} w
-  auto eval = [&](double mu, double& f, double& fp) {
-    for (int r = threadIdx.x; r < N; r += blockDim.x) wv[r] = ga[r] - mu * gb[r];
+  auto band_mv_m = [&](const double* v, int r) {
+    double my = MH[(long long)r * bw1] * v[r];
+    for (int d = 1; d <= bw; ++d) {
+      if (r - d >= 0) my += MH[(long long)r * bw1 + d] * v[r - d];
+      if (r + d < N) my += MH[(long long)(r + d) * bw1 + d] * v[r + d];
+    }
+    return my;
+  };
+  // factor S(mu) and solve S y = w(mu); false if S(mu) is not positive definite
+  auto factor_solve = [&](double mu) {
+    for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) Lb[q] = KH[q] - mu * MH[q];
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      wv[r] = ga[r] - mu * gb[r];
+      y[r] = wv[r];
+    }
     __syncthreads();
-    band_solve(Lb, N, bw, wv, y);
+    if (!band_ldlt(Lb, invD, y, pairs, npair, N, bw, &flag)) return false;
+    band_back(Lb, invD, y, N, bw);
+    return true;
+  };
+  // f(mu) = alpha - mu beta - w^T y, f'(mu) = -beta + 2 g_b^T y - y^T M y
+  auto eval = [&](double mu, double& f, double& fp) {
     double v[3] = {0.0, 0.0, 0.0};
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
-      double my = MH[(long long)r * bw1] * y[r];
-      for (int d = 1; d <= bw; ++d) {
-        if (r - d >= 0) my += MH[(long long)r * bw1 + d] * y[r - d];
-        if (r + d < N) my += MH[(long long)(r + d) * bw1 + d] * y[r + d];
-      }
       v[0] += wv[r] * y[r];
       v[1] += gb[r] * y[r];
-      v[2] += y[r] * my;
+      v[2] += y[r] * band_mv_m(y, r);
     }
     block_sum<3>(v, scratch, red);
     f = alpha - mu * beta - red[0];
     fp = -beta + 2.0 * red[1] - red[2];
   };
-  auto factor = [&](double mu) {
-    for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) Lb[q] = KH[q] - mu * MH[q];
-    __syncthreads();
-    return band_chol(Lb, N, bw, &flag);
-  };
 
-  double mu = alpha / beta, lo = 0.0, hi = INFINITY, mu_final = NAN;
+  // Newton from mu0 = alpha / beta (right of the root: f(mu0) = -w^T S^{-1} w <= 0),
+  // safeguarded by the bracket [lo, hi]; accepted once the step is below 1e-9 relative
+  // (the quadratic error is then at rounding level; y stays the solution at mu).
+  double mu = alpha / beta, lo = 0.0, hi = INFINITY, lam = NAN;
   int it = 0, status = 0;
   bool have = false;
   for (; it < a.max_iter; ++it) {
-    if (!factor(mu)) {
+    if (!factor_solve(mu)) {
       hi = mu;
       mu = 0.5 * (lo + hi);
       have = false;
       continue;
     }
+    have = true;
     double f, fp;
     eval(mu, f, fp);
-    have = true;
-    if (f > 0.0)
-      lo = mu;
-    else
-      hi = mu;
-    // Newton converges quadratically from either side; once its step is below
-    // 1e-13 relative the next one is at the rounding level of f, so accept mu - f/f'.
+    if (f > 0.0) lo = mu;
+    else hi = mu;
     const double step = (fp < 0.0) ? -f / fp : 0.0;
-    const bool conv = fp < 0.0 && fabs(step) <= 1e-13 * fabs(mu);
-    double nmu = (fp < 0.0) ? mu + step : 0.5 * (lo + hi);
-    if (!conv && !(nmu > lo && nmu < hi)) nmu = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * mu;
-    if (!conv && isfinite(hi) && hi - lo <= 1e-15 * hi) nmu = mu;  // bracket exhausted at rounding level
-    if (threadIdx.x == 0) {
-      sh_mu = nmu;
-      sh_done = conv || nmu == mu;
-    }
-    __syncthreads();
-    const double next = sh_mu;
-    const int done = sh_done;
-    __syncthreads();
-    if (done) {
-      mu_final = next;  // y stays the solution at mu (differs by < 1e-13 relative)
+    if (fp < 0.0 && fabs(step) <= 1e-9 * fabs(mu)) {
+      lam = mu + step;
       break;
     }
-    mu = next;
+    double nmu = (fp < 0.0) ? mu + step : 0.5 * (lo + hi);
+    if (!(nmu > lo && nmu < hi)) nmu = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * mu;
+    if (isfinite(hi) && hi - lo <= 1e-15 * hi) {
+      lam = mu;
+      break;
+    }
+    mu = nmu;
   }
   if (it >= a.max_iter) status |= MLEV_ST_RR_NOCONV;
-  if (!(mu_final == mu_final)) mu_final = mu;
-  if (!have) {
-    if (!factor(mu)) status |= MLEV_ST_RR_BREAKDOWN;
-    double f, fp;
-    eval(mu, f, fp);
-  }
+  if (!(lam == lam)) lam = mu;
+  if (!have && !factor_solve(mu)) status |= MLEV_ST_RR_BREAKDOWN;
   // eigenvector c = [-y ; 1], scaled to b(u,u) = 1 and int u > 0
   double v[3] = {0.0, 0.0, 0.0};
   for (int r = threadIdx.x; r < N; r += blockDim.x) {
-    double my = MH[(long long)r * bw1] * y[r];
-    for (int d = 1; d <= bw; ++d) {
-      if (r - d >= 0) my += MH[(long long)r * bw1 + d] * y[r - d];
-      if (r + d < N) my += MH[(long long)(r + d) * bw1 + d] * y[r + d];
-    }
-    v[0] += y[r] * my;
+    v[0] += y[r] * band_mv_m(y, r);
     v[1] += gb[r] * y[r];
     v[2] += y[r];
   }
@@ -566,13 +480,26 @@ __global__ void __launch_bounds__(256) k_rr(DevGeom G, RRArgs a) {
   }
   if (threadIdx.x == 0) {
     a.c0[p] = sc;
-    a.lam[p * (a.n + 1) + a.L] = mu_final;
+    a.lam[p * (a.n + 1) + a.L] = lam;
     a.stat[p * a.stat_stride + MLEV_STAT_RR_IT + a.L] = it + 1;
-    if (!isfinite(mu) || !isfinite(sc)) status |= MLEV_ST_NONFINITE;
+    if (!isfinite(lam) || !isfinite(sc)) status |= MLEV_ST_NONFINITE;
     if (status) atomicOr((unsigned long long*)&a.stat[p * a.stat_stride + MLEV_STAT_FLAGS], (unsigned long long)status);
   }
 }
 
-void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s) { k_rr<<<a.B, 256, 0, s>>>(G, a); }
+// Shared memory of the Rayleigh-Ritz kernel when its band system is kept on chip.
+size_t rr_smem_bytes(int nhb, int bw) {
+  return ((size_t)nhb * (bw + 1) + 5 * (size_t)nhb) * 8 + (size_t)(bw * (bw + 1) / 2) * 4;
+}
+
+void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, kRRSmemMax);
+    attr = true;
+  }
+  const size_t smem = a.smem ? rr_smem_bytes(a.nhb, a.bw) : (size_t)(a.bw * (a.bw + 1) / 2) * 4;
+  k_rr<<<a.B, 256, smem, s>>>(G, a);
+}
 
 }  // namespace mlev

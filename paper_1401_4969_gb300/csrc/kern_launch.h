@@ -17,6 +17,15 @@ void launch_prolong(const DevGeom& G, const Tile* tiles, int n, T* X, cudaStream
 template <typename T>
 void launch_coarsest(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, int sweeps, double omega,
                      cudaStream_t s);
+template <typename T>
+void launch_coarse_inverse(const DevGeom& G, const Tile* tiles, int n, T* inv, int nd_max, cudaStream_t s);
+template <typename T>
+void launch_coarsest_direct(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, const T* inv, int nd_max,
+                            cudaStream_t s);
+size_t coarsest_smem_bytes(int kappa_kind, int nodes, int tsize);  // staged coarsest kernel; limit 220 KiB
+template <typename T>
+void launch_coarsest_smem(const DevGeom& G, const Tile* tiles, int n, int max_nodes, T* X, const T* F, int sweeps,
+                          double omega, cudaStream_t s);
 void launch_job_resnorm(const DevGeom& G, const GlobalLayout& gl, const Tile* tiles, int n, const double* E, int use64,
                         const double* R, double* acc, cudaStream_t s);
 void launch_resnorm_finalize(const double* acc, int B, int m, int subdomains, long long* stat, int stat_stride,
@@ -29,6 +38,16 @@ void launch_accumulate(const DevGeom& G, const Tile* tiles, int n, T* X, double*
 template <typename T>
 void launch_refine_residual(const DevGeom& G, const GlobalLayout& gl, const Tile* tiles, int n, T* F,
                             const double* X64, const double* R, cudaStream_t s);
+
+// ---- fused multigrid (kern_mgfused.cu); nu in {1, 2} ----
+constexpr int kTailSmemMax = 200 * 1024;
+template <typename T>
+void launch_mg_down(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, int nu, double omega, cudaStream_t s);
+template <typename T>
+void launch_mg_up(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, int nu, double omega, cudaStream_t s);
+template <typename T>
+void launch_mg_tail(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, const T* inv, int nd_max, int nlev,
+                    int pre, int post, int csweeps, double omega, int load_x, size_t smem, cudaStream_t s);
 
 // ---- global fields (kern_field.cu) ----
 struct LevelArgs {
@@ -89,7 +108,8 @@ struct RRArgs {
   int nhb, bw;
   const double* KH;
   const double* MH;
-  double* chol;          // [B][nhb][bw+1] scratch
+  double* chol;          // [B][nhb*(bw+1) + 5*nhb] scratch (used when the system does not fit on chip)
+  int smem;              // 1: keep the band system in shared memory
   const double* partials;
   double* lam;           // [B][n+1]
   double* c;             // [B][(ncy+1)(ncx+1)]
@@ -99,5 +119,7 @@ struct RRArgs {
   int max_iter;
 };
 void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s);
+size_t rr_smem_bytes(int nhb, int bw);
+constexpr int kRRSmemMax = 200 * 1024;
 
 }  // namespace mlev

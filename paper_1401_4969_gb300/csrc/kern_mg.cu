@@ -15,6 +15,7 @@
 namespace mlev {
 
 constexpr int TX = 32, TY = 8;
+constexpr int kCoarsestSmemMax = 220 * 1024;
 
 template <typename T, int KK>
 __global__ void __launch_bounds__(256) k_smooth(DevGeom G, const Tile* __restrict__ tiles, T* X, const T* __restrict__ F,
@@ -101,6 +102,129 @@ __global__ void __launch_bounds__(256) k_coarsest(DevGeom G, const Tile* __restr
       __syncthreads();
     }
   }
+}
+
+// Exact solve on the coarsest grid of every subdomain job (its T_H window, at most
+// MLEV_DIRECT_MAX nodes): the matrix of the window's interior nodes (identity rows for
+// nodes that are not unknowns) is assembled in FP64 and inverted by Gauss-Jordan
+// elimination without pivoting (SPD), once per solve; the inverse is kept in T.
+template <typename T, int KK>
+__global__ void __launch_bounds__(256) k_coarse_inverse(DevGeom G, const Tile* __restrict__ tiles, T* inv, int nd_max) {
+  extern __shared__ double smA[];
+  const GridDesc& g = G.grids[tiles[blockIdx.x].grid];
+  const int nx1 = g.nx - 1, ny1 = g.ny - 1, nd = nx1 * ny1;
+  double* A = smA;            // nd x nd
+  double* colk = A + nd * nd; // nd
+  for (int q = threadIdx.x; q < nd * nd; q += blockDim.x) A[q] = 0.0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < nd; r += blockDim.x) {
+    const int i = r % nx1 + 1, j = r / nx1 + 1;
+    if (!is_unknown(G, g, i, j)) {
+      A[r * nd + r] = 1.0;
+      continue;
+    }
+    const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+    A[r * nd + r] = w.e + w.w + w.n + w.s;
+    if (i + 1 <= nx1 && is_unknown(G, g, i + 1, j)) A[r * nd + r + 1] = -w.e;
+    if (i - 1 >= 1 && is_unknown(G, g, i - 1, j)) A[r * nd + r - 1] = -w.w;
+    if (j + 1 <= ny1 && is_unknown(G, g, i, j + 1)) A[r * nd + r + nx1] = -w.n;
+    if (j - 1 >= 1 && is_unknown(G, g, i, j - 1)) A[r * nd + r - nx1] = -w.s;
+  }
+  for (int k = 0; k < nd; ++k) {
+    __syncthreads();
+    const double ip = 1.0 / A[k * nd + k];
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) colk[i] = (i == k) ? 0.0 : A[i * nd + k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < nd; c += blockDim.x) A[k * nd + c] = (c == k ? 1.0 : A[k * nd + c]) * ip;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nd * nd; q += blockDim.x) {
+      const int i = q / nd, c = q % nd;
+      if (i == k) continue;
+      A[q] = (c == k ? 0.0 : A[q]) - colk[i] * A[k * nd + c];
+    }
+  }
+  __syncthreads();
+  T* out = inv + (long long)g.job * nd_max * nd_max;
+  for (int q = threadIdx.x; q < nd * nd; q += blockDim.x) out[q] = (T)A[q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_coarsest_direct(DevGeom G, const Tile* __restrict__ tiles, T* X,
+                                                         const T* __restrict__ F, const T* __restrict__ inv,
+                                                         int nd_max) {
+  extern __shared__ unsigned char smraw[];
+  T* f = reinterpret_cast<T*>(smraw);
+  const GridDesc& g = G.grids[tiles[blockIdx.x].grid];
+  const int nx1 = g.nx - 1, ny1 = g.ny - 1, nd = nx1 * ny1;
+  for (int r = threadIdx.x; r < nd; r += blockDim.x) {
+    const int i = r % nx1 + 1, j = r / nx1 + 1;
+    f[r] = is_unknown(G, g, i, j) ? F[g.off + (long long)j * g.pitch + i] : (T)0;
+  }
+  __syncthreads();
+  const T* A = inv + (long long)g.job * nd_max * nd_max;
+  for (int r = threadIdx.x; r < nd; r += blockDim.x) {
+    const int i = r % nx1 + 1, j = r / nx1 + 1;
+    T sacc = (T)0;
+    for (int c = 0; c < nd; ++c) sacc += A[r * nd + c] * f[c];
+    X[g.off + (long long)j * g.pitch + i] = is_unknown(G, g, i, j) ? sacc : (T)0;
+  }
+}
+
+// Coarsest grid staged in shared memory (the strip's T_{h_2} window): per-node weights
+// and inverse diagonals are computed once, then `sweeps` red-black sweeps run from
+// shared memory with one block of 1024 threads per job.
+template <typename T, int KK>
+__global__ void __launch_bounds__(1024) k_coarsest_smem(DevGeom G, const Tile* __restrict__ tiles, T* X,
+                                                        const T* __restrict__ F, int sweeps, T omega) {
+  constexpr bool kOne = (KK == MLEV_KAPPA_ONE);  // unit weights: store none
+  extern __shared__ unsigned char smraw[];
+  const GridDesc& g = G.grids[tiles[blockIdx.x].grid];
+  const int W = g.nx + 1, nn = W * (g.ny + 1);
+  T* x = reinterpret_cast<T*>(smraw);
+  T* f = x + nn;
+  T* idg = f + nn;  // inverse diagonal; 0 marks a node that is not an unknown
+  T* we = idg + nn;
+  T* ww = we + (kOne ? 0 : nn);
+  T* wn = ww + (kOne ? 0 : nn);
+  T* wsx = wn + (kOne ? 0 : nn);
+  // block 32 x 32: rows by threadIdx.y, columns by threadIdx.x
+  for (int j = threadIdx.y; j <= g.ny; j += blockDim.y)
+    for (int i = threadIdx.x; i <= g.nx; i += blockDim.x) {
+      const int q = j * W + i;
+      const long long c = (long long)j * g.pitch + i;
+      x[q] = X[g.off + c];
+      if (is_unknown(G, g, i, j)) {
+        const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+        f[q] = F[g.off + c];
+        idg[q] = (T)(1.0 / (w.e + w.w + w.n + w.s));
+        if (!kOne) {
+          we[q] = (T)w.e; ww[q] = (T)w.w; wn[q] = (T)w.n; wsx[q] = (T)w.s;
+        }
+      } else {
+        f[q] = (T)0;
+        idg[q] = (T)0;
+      }
+    }
+  __syncthreads();
+  for (int s = 0; s < sweeps; ++s)
+    for (int color = 0; color < 2; ++color) {
+      for (int j = 1 + threadIdx.y; j < g.ny; j += blockDim.y) {
+        const int i0 = ((color + j) & 1) ? 1 : 2;
+        for (int i = i0 + 2 * threadIdx.x; i < g.nx; i += 2 * blockDim.x) {
+          const int q = j * W + i;
+          if (idg[q] == (T)0) continue;
+          T v;
+          if (kOne)
+            v = f[q] + x[q + 1] + x[q - 1] + x[q + W] + x[q - W];
+          else
+            v = f[q] + we[q] * x[q + 1] + ww[q] * x[q - 1] + wn[q] * x[q + W] + wsx[q] * x[q - W];
+          x[q] += omega * (v * idg[q] - x[q]);
+        }
+      }
+      __syncthreads();
+    }
+  for (int j = threadIdx.y; j <= g.ny; j += blockDim.y)
+    for (int i = threadIdx.x; i <= g.nx; i += blockDim.x) X[g.off + (long long)j * g.pitch + i] = x[j * W + i];
 }
 
 // Finest grids of subdomain jobs: f = R (global residual of Eq. Aux_Problem restricted
@@ -254,6 +378,45 @@ void launch_refine_residual(const DevGeom& G, const GlobalLayout& gl, const Tile
   MLEV_DISPATCH_KK(G.kap.kind, (k_refine_residual<T, KK><<<n, dim3(TX, TY), 0, s>>>(G, gl, tiles, F, X64, R)));
 }
 
+template <typename T>
+void launch_coarse_inverse(const DevGeom& G, const Tile* tiles, int n, T* inv, int nd_max, cudaStream_t s) {
+  if (!n) return;
+  const size_t smem = ((size_t)nd_max * nd_max + nd_max) * sizeof(double);
+  MLEV_DISPATCH_KK(G.kap.kind, ({
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_coarse_inverse<T, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr = true;
+    }
+    k_coarse_inverse<T, KK><<<n, 256, smem, s>>>(G, tiles, inv, nd_max);
+  }));
+}
+template <typename T>
+void launch_coarsest_direct(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, const T* inv, int nd_max,
+                            cudaStream_t s) {
+  if (!n) return;
+  k_coarsest_direct<T><<<n, 128, (size_t)nd_max * sizeof(T), s>>>(G, tiles, X, F, inv, nd_max);
+}
+// Bytes of shared memory the staged coarsest kernel needs for a grid of `nodes` nodes.
+size_t coarsest_smem_bytes(int kappa_kind, int nodes, int tsize) {
+  return (size_t)(kappa_kind == MLEV_KAPPA_ONE ? 3 : 7) * nodes * tsize;
+}
+
+template <typename T>
+void launch_coarsest_smem(const DevGeom& G, const Tile* tiles, int n, int max_nodes, T* X, const T* F, int sweeps,
+                          double omega, cudaStream_t s) {
+  if (!n) return;
+  const size_t smem = coarsest_smem_bytes(G.kap.kind, max_nodes, sizeof(T));
+  MLEV_DISPATCH_KK(G.kap.kind, ({
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_coarsest_smem<T, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCoarsestSmemMax);
+      attr = true;
+    }
+    k_coarsest_smem<T, KK><<<n, dim3(32, 32), smem, s>>>(G, tiles, X, F, sweeps, (T)omega);
+  }));
+}
+
 void launch_job_resnorm(const DevGeom& G, const GlobalLayout& gl, const Tile* tiles, int n, const double* E, int use64,
                         const double* R, double* acc, cudaStream_t s) {
   if (!n) return;
@@ -273,7 +436,12 @@ void launch_resnorm_finalize(const double* acc, int B, int m, int subdomains, lo
                                  const double*, cudaStream_t);                                                   \
   template void launch_accumulate<T>(const DevGeom&, const Tile*, int, T*, double*, cudaStream_t);               \
   template void launch_refine_residual<T>(const DevGeom&, const GlobalLayout&, const Tile*, int, T*,             \
-                                          const double*, const double*, cudaStream_t);
+                                          const double*, const double*, cudaStream_t);                           \
+  template void launch_coarse_inverse<T>(const DevGeom&, const Tile*, int, T*, int, cudaStream_t);               \
+  template void launch_coarsest_direct<T>(const DevGeom&, const Tile*, int, T*, const T*, const T*, int,         \
+                                          cudaStream_t);                                                         \
+  template void launch_coarsest_smem<T>(const DevGeom&, const Tile*, int, int, T*, const T*, int, double,        \
+                                        cudaStream_t);
 MLEV_INST(float)
 MLEV_INST(double)
 

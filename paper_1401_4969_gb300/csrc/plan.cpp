@@ -116,6 +116,22 @@ long long grid_unknowns(const Plan& p, const GridDesc& g) {
   return cnt;
 }
 
+// Does the w x h block of nodes at (x0, y0) of grid g contain an unknown?
+static bool block_has_unknown(const Plan& p, const GridDesc& g, int x0, int y0, int w, int h) {
+  const int xa = std::max(1, x0), xb = std::min(g.nx - 1, x0 + w - 1);
+  const int ya = std::max(1, y0), yb = std::min(g.ny - 1, y0 + h - 1);
+  if (xa > xb || ya > yb) return false;
+  if (g.full) return true;
+  const uint8_t* reg = p.regions.data() + g.roff;
+  const int s = g.rshift;
+  for (int j = ya; j <= yb; ++j)
+    for (int i = xa; i <= xb; ++i) {
+      const int a = (i - 1) >> s, b = i >> s, c = (j - 1) >> s, d = j >> s;
+      if (reg[c * g.rnx + a] && reg[c * g.rnx + b] && reg[d * g.rnx + a] && reg[d * g.rnx + b]) return true;
+    }
+  return false;
+}
+
 std::string Plan::build(const mlev_opts& o) {
   if (!ready()) return "STATE: set domain, partition, levels and forms before solving";
   tsize = o.precision == MLEV_PREC_FP64 ? 8 : 4;
@@ -174,6 +190,11 @@ std::string Plan::build(const mlev_opts& o) {
   }
   nhb = (ncx - 1) * (ncy - 1);
   bw = ncx;
+  nd_max = 0;
+  for (int j = 0; j < m; ++j) nd_max = std::max(nd_max, (Om[j][2] - Om[j][0] - 1) * (Om[j][3] - Om[j][1] - 1));
+  nd_max = std::max(nd_max, 1);
+  sub_direct = nd_max <= kDirectMax;
+  strip_coarse_nodes = (4 * ncx + 1) * (4 * ncy + 1);
 
   // ---- region grids ----
   regions.clear();
@@ -334,6 +355,53 @@ std::string Plan::build(const mlev_opts& o) {
     P.sub_coarsest = list_of(sub_coarse);
     P.sub_top = list_of(sub_topg);
     P.strip_coarsest = list_of(strip_coarse);
+    // ---- fused multigrid: tail depth and tile lists
+    auto tail_bytes = [&](int gi, int nlev, int extra) {
+      long long tot = 0;
+      for (int k = 0; k < nlev; ++k) {
+        const GridDesc& g = grids[gi + k];
+        tot += (long long)(g.nx + 1) * (g.ny + 1);
+        tot = (tot + 1) & ~1LL;
+      }
+      return (size_t)(2 * tot + extra) * tsize + (size_t)tot;  // x, f, dense-solve buffer, unknown mask
+    };
+    auto plan_fused = [&](const std::vector<std::vector<int>>& by_depth, std::vector<TileList>& fl, int& dt,
+                          TileList& tail, size_t& tail_smem, int extra) {
+      const int D = (int)by_depth.size() - 1;
+      dt = D + 1;
+      tail_smem = 0;
+      for (int d = 0; d <= D; ++d) {
+        size_t need = 0;
+        for (int gi : by_depth[d]) need = std::max(need, tail_bytes(gi, D - d + 1, extra));
+        if (need <= kTailBudget) {
+          dt = d;
+          tail_smem = need;
+          break;
+        }
+      }
+      fl.assign(std::min(dt, D + 1), TileList());
+      for (int d = 0; d < (int)fl.size(); ++d) {
+        fl[d].off = (long long)tiles.size();
+        for (int gi : by_depth[d]) {
+          const GridDesc& g = grids[gi];
+          for (int y = 0; y <= g.ny; y += kFusedTile)
+            for (int x = 0; x <= g.nx; x += kFusedTile)
+              if (block_has_unknown(*this, g, x, y, kFusedTile, kFusedTile)) tiles.push_back(Tile{gi, x, y});
+          fl[d].unk += unk_of(gi);
+        }
+        fl[d].count = (int)((long long)tiles.size() - fl[d].off);
+      }
+      if (dt <= D) {
+        tail.off = (long long)tiles.size();
+        for (int gi : by_depth[dt]) {
+          tiles.push_back(Tile{gi, 0, 0});
+          tail.unk += unk_of(gi);
+        }
+        tail.count = (int)by_depth[dt].size();
+      }
+    };
+    plan_fused(sub_by_depth, P.sub_f, P.sub_dt, P.sub_tail, P.sub_tail_smem, sub_direct ? nd_max : 0);
+    plan_fused(strip_by_depth, P.strip_f, P.strip_dt, P.strip_tail, P.strip_tail_smem, 0);
     P.pool_elems = pool;
     P.pool64_elems = pool64;
     // unknown counts per problem (reports and the traffic model)
@@ -435,9 +503,10 @@ std::string Plan::build(const mlev_opts& o) {
   take(w_c0, (size_t)B * 8);
   take(w_stat, (size_t)B * mlev_stat_stride(n) * 8);
   take(w_jobnorm, (size_t)B * (m + 1) * 2 * 8);
-  take(w_chol, (size_t)B * ((size_t)nhb * (bw + 1) + 4 * (size_t)nhb) * 8);
+  take(w_chol, (size_t)B * ((size_t)nhb * (bw + 1) + 5 * (size_t)nhb) * 8);
   take(w_out_lam, (size_t)B * 8);
   take(w_out_u, (size_t)B * (lvl_nx(n) + 1) * (lvl_ny(n) + 1) * 8);
+  take(w_cinv, sub_direct ? (size_t)B * m * nd_max * nd_max * tsize : 0);
   ws_bytes = cur;
   return "";
 }

@@ -36,7 +36,17 @@ struct LevelPlan {                      // correction level L = k + 1
   long long pool64_elems = 0;           // X64 pool elements used
   long long n_local = 0, n_strip = 0;   // unknowns per problem
   long long n_free = 0;                 // free nodes of the level-L lattice per problem
+  // fused multigrid: 64x64 tiles (only tiles with unknowns) for depths above the tail,
+  // and the tail (one block per job from depth *_dt down to the coarsest grid)
+  std::vector<TileList> sub_f, strip_f;
+  int sub_dt = 0, strip_dt = 0;          // first tail depth (= number of depths + 1 if no tail fits)
+  TileList sub_tail, strip_tail;
+  size_t sub_tail_smem = 0, strip_tail_smem = 0;
 };
+
+constexpr int kDirectMax = 128;         // largest coarsest window solved with a dense inverse
+constexpr int kFusedTile = 64;          // output tile edge of the fused down / up kernels
+constexpr size_t kTailBudget = 160 * 1024;  // shared memory allowed to one tail block
 
 struct Plan {
   // ---- inputs ----
@@ -72,12 +82,15 @@ struct Plan {
   long long n_fine = 0;
   int n_coarse = 0;
   int nhb = 0, bw = 0;                     // coarse band system: rows (ncx-1)(ncy-1), half bandwidth
+  int sub_direct = 0;                      // subdomain coarsest grids solved by a dense inverse
+  int nd_max = 0;                          // largest coarsest-window size (interior nodes) of a subdomain
+  int strip_coarse_nodes = 0;              // nodes of the strip's coarsest (T_{h_2}) grid
 
   // ---- workspace layout (depends on opts) ----
   int tsize = 4;
   Span w_grids, w_tiles, w_regions, w_qlabel, w_cellin, w_subtop;
   Span w_kstage, w_klvl, w_band, w_ut[2], w_uin, w_r, w_l1vec, w_l1pool[2];
-  Span w_x, w_f, w_x64, w_aug, w_lam, w_c, w_c0, w_stat, w_jobnorm, w_chol, w_out_lam, w_out_u;
+  Span w_x, w_f, w_x64, w_aug, w_lam, w_c, w_c0, w_stat, w_jobnorm, w_chol, w_out_lam, w_out_u, w_cinv;
   size_t ws_bytes = 0;
   size_t tables_bytes = 0;
   KappaDev kap_template{};  // offsets relative to the workspace base
