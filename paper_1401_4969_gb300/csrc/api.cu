@@ -1,4 +1,6 @@
 // C ABI of the mlev library and the launch sequence of Algorithm 4.2.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -266,6 +268,8 @@ struct Launcher {
     G.qlabel = at<int16_t>(ws, P.w_qlabel);
     G.cell_in = at<uint8_t>(ws, P.w_cellin);
     G.sub_top = at<int>(ws, P.w_subtop);
+    G.tmaps = at<unsigned char>(ws, P.w_tmaps);
+    G.status = reinterpret_cast<unsigned long long*>(at<long long>(ws, P.w_stat) + MLEV_STAT_FLAGS);
     G.ncx = P.ncx;
     G.ncy = P.ncy;
     G.m = P.m;
@@ -445,6 +449,53 @@ int prepare(mlev_ctx* ctx, const mlev_opts* o, void* ws, size_t ws_bytes) {
   return MLEV_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up through the runtime (the library does
+// not link libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor maps of the grids read by the fused kernels: boxes over the x and f pools of the
+// grid (pitched 2-D arrays of (nx+1) x (ny+1) nodes); out-of-range boxes read zeros.
+std::string encode_tensor_maps(const Plan& P, void* ws, char* host) {
+  if (!P.n_tmap_grids) return "";
+  auto enc = tensor_map_encoder();
+  if (!enc) return "cuTensorMapEncodeTiled is not available from the driver";
+  const CUtensorMapDataType dt = P.tsize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host + P.w_tmaps.off);
+  char* xbase = static_cast<char*>(ws) + P.w_x.off;
+  char* fbase = static_cast<char*>(ws) + P.w_f.off;
+  for (const GridDesc& g : P.grids) {
+    if (g.tmap < 0) continue;
+    const cuuint64_t dims[2] = {(cuuint64_t)g.nx + 1, (cuuint64_t)g.ny + 1};
+    const cuuint64_t strides[1] = {(cuuint64_t)g.pitch * P.tsize};
+    const cuuint32_t fbox[2] = {MLEV_TMA_FBW, MLEV_TMA_FBH}, cbox[2] = {MLEV_TMA_CBW, MLEV_TMA_CBH};
+    const cuuint32_t es[2] = {1, 1};
+    void* xa = xbase + g.off * P.tsize;
+    void* fa = fbase + g.off * P.tsize;
+    CUresult r0 = enc(&maps[g.tmap + 0], dt, 2, xa, dims, strides, fbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r1 = enc(&maps[g.tmap + 1], dt, 2, fa, dims, strides, fbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r2 = enc(&maps[g.tmap + 2], dt, 2, xa, dims, strides, cbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r0 != CUDA_SUCCESS || r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
+      return "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r0) + "/" + std::to_string((int)r1) + "/" +
+             std::to_string((int)r2) + ")";
+  }
+  return "";
+}
+
 int upload_tables(mlev_ctx* ctx, void* ws, cudaStream_t s, bool force) {
   Plan& P = ctx->plan;
   const long long key = ctx->version * 2 + ctx->built_precision;
@@ -459,6 +510,8 @@ int upload_tables(mlev_ctx* ctx, void* ws, cudaStream_t s, bool force) {
   put(P.w_qlabel, P.qlabel.data(), P.qlabel.size() * sizeof(int16_t));
   put(P.w_cellin, P.cell_in.data(), P.cell_in.size());
   put(P.w_subtop, P.sub_top.data(), P.sub_top.size() * sizeof(int));
+  std::string terr = encode_tensor_maps(P, ws, host.data());
+  if (!terr.empty()) return fail(ctx, MLEV_ECUDA, terr);
   CK(cudaMemcpyAsync(ws, host.data(), host.size(), cudaMemcpyHostToDevice, s));
   ctx->io_h2d += (long long)host.size();
   if (!P.kappa_on_device && !P.kappa_host.empty()) {
@@ -510,6 +563,8 @@ int fill_report(mlev_ctx* ctx, void* ws, cudaStream_t s, mlev_report* rep) {
   rep->kernel_launches = ctx->launches;
   rep->h2d_bytes = ctx->io_h2d;
   rep->d2h_bytes = ctx->io_d2h;
+  if (flags & MLEV_ST_TIMEOUT)
+    return fail(ctx, MLEV_ETIMEOUT, "a bounded device-side wait gave up (status flags " + std::to_string(flags) + ")");
   if (flags & (MLEV_ST_LEVEL1_NOCONV | MLEV_ST_RR_NOCONV))
     return fail(ctx, MLEV_ENOCONV, "an iteration reached its cap (status flags " + std::to_string(flags) + ")");
   if (flags) return fail(ctx, MLEV_ENOCONV, "numerical breakdown (status flags " + std::to_string(flags) + ")");

@@ -85,11 +85,15 @@ __device__ void blk_direct(const DevGeom& G, const GridDesc& g, T* X, const T* F
     fbuf[r] = is_unknown(G, g, i, j) ? F[g.off + (long long)j * g.pitch + i] : (T)0;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < nd; r += blockDim.x) {
-    const int j = r / nx1 + 1, i = r - (j - 1) * nx1 + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < nd; r += nw) {  // one warp per row of the inverse
     T acc = (T)0;
-    for (int c = 0; c < nd; ++c) acc += inv[r * nd + c] * fbuf[c];
-    X[g.off + (long long)j * g.pitch + i] = is_unknown(G, g, i, j) ? acc : (T)0;
+    for (int c = lane; c < nd; c += 32) acc += inv[r * nd + c] * fbuf[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const int j = r / nx1 + 1, i = r - (j - 1) * nx1 + 1;
+      X[g.off + (long long)j * g.pitch + i] = is_unknown(G, g, i, j) ? acc : (T)0;
+    }
   }
   __syncthreads();
 }

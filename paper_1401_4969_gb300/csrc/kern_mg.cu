@@ -162,11 +162,15 @@ __global__ void __launch_bounds__(128) k_coarsest_direct(DevGeom G, const Tile* 
   }
   __syncthreads();
   const T* A = inv + (long long)g.job * nd_max * nd_max;
-  for (int r = threadIdx.x; r < nd; r += blockDim.x) {
-    const int i = r % nx1 + 1, j = r / nx1 + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < nd; r += nw) {  // one warp per row of the inverse
     T sacc = (T)0;
-    for (int c = 0; c < nd; ++c) sacc += A[r * nd + c] * f[c];
-    X[g.off + (long long)j * g.pitch + i] = is_unknown(G, g, i, j) ? sacc : (T)0;
+    for (int c = lane; c < nd; c += 32) sacc += A[r * nd + c] * f[c];
+    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+    if (lane == 0) {
+      const int i = r % nx1 + 1, j = r / nx1 + 1;
+      X[g.off + (long long)j * g.pitch + i] = is_unknown(G, g, i, j) ? sacc : (T)0;
+    }
   }
 }
 

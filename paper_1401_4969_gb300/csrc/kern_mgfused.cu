@@ -18,67 +18,145 @@ namespace mlev {
 
 constexpr int FT = 64;  // output tile edge of the fused kernels (nodes)
 
-// Thread block of the fused kernels: 32 x 8 threads; loops below walk rows with threadIdx.y
-// and, within a row, either every node (stride 32) or the nodes of one colour (stride 64).
+// ---------------------------------------------------------------- TMA / mbarrier (inline PTX)
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 2-D tiled bulk tensor copy global -> shared; x must be a multiple of 16 bytes / element size.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"((unsigned long long)tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmap_acquire(const void* tmap) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((unsigned long long)tmap) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase 0 of the barrier: gives up after ~2^22 polls and flags a timeout
+// (the block then computes on whatever arrived; the solve reports MLEV_ETIMEOUT).
+__device__ __forceinline__ void mbar_wait0(unsigned long long* bar, unsigned long long* status) {
+  for (unsigned it = 0; !mbar_try_wait(bar, 0); ++it)
+    if (it > (1u << 22)) {
+      if (threadIdx.x == 0 && threadIdx.y == 0 && status) atomicOr(status, (unsigned long long)MLEV_ST_TIMEOUT);
+      break;
+    }
+}
+
+__device__ __forceinline__ const void* grid_map(const DevGeom& G, const GridDesc& g, int which) {
+  return G.tmaps + (long long)(g.tmap + which) * MLEV_TMAP_BYTES;
+}
+
+// Thread block of the fused kernels: 32 x 8 threads; loops walk rows with threadIdx.y and,
+// within a row, either every node (stride 32) or the nodes of one colour (stride 64).
+// Tiles live in the TMA box layout: row pitch SW = MLEV_TMA_FBW; region node (a, b) is at
+// q = (b + oy) * SW + a + ox.
 template <typename T, int KK>
 __device__ __forceinline__ void tile_half_sweep(const DevGeom& G, const GridDesc& g, T* xs, const T* fs,
-                                                const uint8_t* uk, int RW, int rx0, int ry0, int lo, int hi, int color,
-                                                T omega) {
+                                                const uint8_t* uk, int ox, int oy, int rx0, int ry0, int lo, int hi,
+                                                int color, T omega) {
+  constexpr int SW = MLEV_TMA_FBW;
   for (int b = lo + threadIdx.y; b <= hi; b += blockDim.y) {
-    // first a >= lo in this row with (rx0 + a + ry0 + b) even == colour parity
     const int a0 = lo + (((rx0 + lo + ry0 + b) & 1) != color);
     for (int a = a0 + 2 * threadIdx.x; a <= hi; a += 2 * blockDim.x) {
-      const int q = b * RW + a;
+      const int q = (b + oy) * SW + a + ox;
       if (!uk[q]) continue;
       const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + rx0 + a, g.oy + ry0 + b);
-      const T v = fs[q] + (T)w.e * xs[q + 1] + (T)w.w * xs[q - 1] + (T)w.n * xs[q + RW] + (T)w.s * xs[q - RW];
+      const T v = fs[q] + (T)w.e * xs[q + 1] + (T)w.w * xs[q - 1] + (T)w.n * xs[q + SW] + (T)w.s * xs[q - SW];
       xs[q] += omega * (v / (T)(w.e + w.w + w.n + w.s) - xs[q]);
     }
   }
 }
 
+// Unknown mask of the whole fine box (computed while the TMA copies are in flight).
+__device__ __forceinline__ void box_mask(const DevGeom& G, const GridDesc& g, uint8_t* uk, int fx0, int fy0) {
+  for (int r = threadIdx.y; r < MLEV_TMA_FBH; r += blockDim.y)
+    for (int c = threadIdx.x; c < MLEV_TMA_FBW; c += blockDim.x)
+      uk[r * MLEV_TMA_FBW + c] = is_unknown(G, g, fx0 + c, fy0 + r);
+}
+
+template <typename T>
+struct FusedSmem {  // byte offsets inside the dynamic shared memory (128-byte aligned arrays)
+  static constexpr int FBOX = MLEV_TMA_FBW * MLEV_TMA_FBH;
+  static constexpr int CBOX = MLEV_TMA_CBW * MLEV_TMA_CBH;
+  static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
+  static constexpr size_t xs = 0;
+  static constexpr size_t fs = al(xs + FBOX * sizeof(T));
+  static constexpr size_t xc = al(fs + FBOX * sizeof(T));
+  static constexpr size_t uk = al(xc + CBOX * sizeof(T));
+  static constexpr size_t total = al(uk + FBOX);
+};
+
 template <typename T, int KK, int NU>
 __global__ void __launch_bounds__(256) k_mg_down(DevGeom G, const Tile* __restrict__ tiles, T* X, T* F, T omega) {
   constexpr int HALO = 2 * NU + 2;
   constexpr int RW = FT + 2 * HALO;
-  extern __shared__ unsigned char sm_raw[];
-  T* xs = reinterpret_cast<T*>(sm_raw);
-  T* fs = xs + RW * RW;
-  uint8_t* uk = reinterpret_cast<uint8_t*>(fs + RW * RW);
+  constexpr int SW = MLEV_TMA_FBW, OX = MLEV_TMA_FOX - HALO, OY = MLEV_TMA_FOY - HALO;
+  using L = FusedSmem<T>;
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ unsigned long long bar;
+  unsigned char* sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);  // TMA destinations: 128-byte aligned
+  T* xs = reinterpret_cast<T*>(sm + L::xs);
+  T* fs = reinterpret_cast<T*>(sm + L::fs);
+  uint8_t* uk = sm + L::uk;
   const Tile t = tiles[blockIdx.x];
   const GridDesc& g = G.grids[t.grid];
   const GridDesc& gc = G.grids[t.grid + 1];
   const int rx0 = t.x0 - HALO, ry0 = t.y0 - HALO;
-  for (int b = threadIdx.y; b < RW; b += blockDim.y)
-    for (int a = threadIdx.x; a < RW; a += blockDim.x) {
-      const int q = b * RW + a, i = rx0 + a, j = ry0 + b;
-      const bool in = i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
-      const bool u = is_unknown(G, g, i, j);
-      const long long c = (long long)j * g.pitch + i;
-      xs[q] = in ? X[g.off + c] : (T)0;
-      fs[q] = u ? F[g.off + c] : (T)0;
-      uk[q] = u;
-    }
+  const int fx0 = t.x0 - MLEV_TMA_FOX, fy0 = t.y0 - MLEV_TMA_FOY;
+  const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+  if (lead) mbar_init(&bar);
+  __syncthreads();
+  if (lead) {
+    const void* mx = grid_map(G, g, 0);
+    const void* mf = grid_map(G, g, 1);
+    tmap_acquire(mx);
+    tmap_acquire(mf);
+    mbar_expect_tx(&bar, 2u * L::FBOX * sizeof(T));
+    tma_load_2d(xs, mx, fx0, fy0, &bar);
+    tma_load_2d(fs, mf, fx0, fy0, &bar);
+  }
+  box_mask(G, g, uk, fx0, fy0);
+  mbar_wait0(&bar, G.status);
   __syncthreads();
   for (int s = 0; s < 2 * NU; ++s) {
-    tile_half_sweep<T, KK>(G, g, xs, fs, uk, RW, rx0, ry0, s + 1, RW - 2 - s, s & 1, omega);
+    tile_half_sweep<T, KK>(G, g, xs, fs, uk, OX, OY, rx0, ry0, s + 1, RW - 2 - s, s & 1, omega);
     __syncthreads();
   }
-  {  // residual in place where the restriction needs it
+  {  // residual in place where the restriction needs it (0 off the unknowns)
     const int lo = 2 * NU + 1, hi = RW - 2 - 2 * NU;
     for (int b = lo + threadIdx.y; b <= hi; b += blockDim.y)
       for (int a = lo + threadIdx.x; a <= hi; a += blockDim.x) {
-        const int q = b * RW + a;
-        if (!uk[q]) continue;
+        const int q = (b + OY) * SW + a + OX;
+        if (!uk[q]) {
+          fs[q] = (T)0;
+          continue;
+        }
         const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + rx0 + a, g.oy + ry0 + b);
         fs[q] -= (T)(w.e + w.w + w.n + w.s) * xs[q] - (T)w.e * xs[q + 1] - (T)w.w * xs[q - 1] -
-                 (T)w.n * xs[q + RW] - (T)w.s * xs[q - RW];
+                 (T)w.n * xs[q + SW] - (T)w.s * xs[q - SW];
       }
   }
   __syncthreads();
   for (int bb = threadIdx.y; bb < FT; bb += blockDim.y)
     for (int aa = threadIdx.x; aa < FT; aa += blockDim.x) {
-      const int i = t.x0 + aa, j = t.y0 + bb, q = (bb + HALO) * RW + aa + HALO;
+      const int i = t.x0 + aa, j = t.y0 + bb, q = (bb + MLEV_TMA_FOY) * SW + aa + MLEV_TMA_FOX;
       if (i <= g.nx && j <= g.ny && uk[q]) X[g.off + (long long)j * g.pitch + i] = xs[q];
     }
   constexpr int CT = FT / 2;
@@ -89,9 +167,9 @@ __global__ void __launch_bounds__(256) k_mg_down(DevGeom G, const Tile* __restri
       const long long cc = (long long)J * gc.pitch + I;
       X[gc.off + cc] = (T)0;
       if (!is_unknown(G, gc, I, J)) continue;
-      const int q = (2 * J - ry0) * RW + (2 * I - rx0);
+      const int q = (2 * J - fy0) * SW + (2 * I - fx0);
       F[gc.off + cc] =
-          fs[q] + (T)0.5 * (fs[q + 1] + fs[q - 1] + fs[q + RW] + fs[q - RW] + fs[q + RW + 1] + fs[q - RW - 1]);
+          fs[q] + (T)0.5 * (fs[q + 1] + fs[q - 1] + fs[q + SW] + fs[q - SW] + fs[q + SW + 1] + fs[q - SW - 1]);
     }
 }
 
@@ -100,42 +178,62 @@ __global__ void __launch_bounds__(256) k_mg_up(DevGeom G, const Tile* __restrict
                                                T omega) {
   constexpr int HALO = 2 * NU;
   constexpr int RW = FT + 2 * HALO;
-  extern __shared__ unsigned char sm_raw[];
-  T* xs = reinterpret_cast<T*>(sm_raw);
-  T* fs = xs + RW * RW;
-  uint8_t* uk = reinterpret_cast<uint8_t*>(fs + RW * RW);
+  constexpr int SW = MLEV_TMA_FBW, OX = MLEV_TMA_FOX - HALO, OY = MLEV_TMA_FOY - HALO;
+  constexpr int CW = MLEV_TMA_CBW;
+  using L = FusedSmem<T>;
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  __shared__ unsigned long long bar;
+  unsigned char* sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u);  // TMA destinations: 128-byte aligned
+  T* xs = reinterpret_cast<T*>(sm + L::xs);
+  T* fs = reinterpret_cast<T*>(sm + L::fs);
+  T* xc = reinterpret_cast<T*>(sm + L::xc);
+  uint8_t* uk = sm + L::uk;
   const Tile t = tiles[blockIdx.x];
   const GridDesc& g = G.grids[t.grid];
   const GridDesc& gc = G.grids[t.grid + 1];
-  const T* xc = X + gc.off;
   const int rx0 = t.x0 - HALO, ry0 = t.y0 - HALO;
+  const int fx0 = t.x0 - MLEV_TMA_FOX, fy0 = t.y0 - MLEV_TMA_FOY;
+  const int cx0 = (t.x0 >> 1) - MLEV_TMA_COX, cy0 = (t.y0 >> 1) - MLEV_TMA_COY;
+  const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+  if (lead) mbar_init(&bar);
+  __syncthreads();
+  if (lead) {
+    const void* mx = grid_map(G, g, 0);
+    const void* mf = grid_map(G, g, 1);
+    const void* mc = grid_map(G, gc, 2);
+    tmap_acquire(mx);
+    tmap_acquire(mf);
+    tmap_acquire(mc);
+    mbar_expect_tx(&bar, (2u * L::FBOX + L::CBOX) * sizeof(T));
+    tma_load_2d(xs, mx, fx0, fy0, &bar);
+    tma_load_2d(fs, mf, fx0, fy0, &bar);
+    tma_load_2d(xc, mc, cx0, cy0, &bar);
+  }
+  box_mask(G, g, uk, fx0, fy0);
+  mbar_wait0(&bar, G.status);
+  __syncthreads();
+  // x += P x_c on the region (exact P1 interpolation on the SW-NE mesh)
   for (int b = threadIdx.y; b < RW; b += blockDim.y)
     for (int a = threadIdx.x; a < RW; a += blockDim.x) {
-      const int q = b * RW + a, i = rx0 + a, j = ry0 + b;
-      const bool in = i >= 0 && j >= 0 && i <= g.nx && j <= g.ny;
-      const bool u = is_unknown(G, g, i, j);
-      const long long c = (long long)j * g.pitch + i;
-      T x = in ? X[g.off + c] : (T)0;
-      if (u) {  // x += P x_c (exact P1 interpolation on the SW-NE mesh)
-        const int I = i >> 1, J = j >> 1;
-        const long long cj = (long long)J * gc.pitch + I;
-        if (!(i & 1) && !(j & 1)) x += xc[cj];
-        else if ((i & 1) && !(j & 1)) x += (T)0.5 * (xc[cj] + xc[cj + 1]);
-        else if (!(i & 1) && (j & 1)) x += (T)0.5 * (xc[cj] + xc[cj + gc.pitch]);
-        else x += (T)0.5 * (xc[cj] + xc[cj + gc.pitch + 1]);
-      }
-      xs[q] = x;
-      fs[q] = u ? F[g.off + c] : (T)0;
-      uk[q] = u;
+      const int q = (b + OY) * SW + a + OX;
+      if (!uk[q]) continue;
+      const int i = rx0 + a, j = ry0 + b;
+      const int c = ((j >> 1) - cy0) * CW + ((i >> 1) - cx0);
+      T v;
+      if (!(i & 1) && !(j & 1)) v = xc[c];
+      else if ((i & 1) && !(j & 1)) v = (T)0.5 * (xc[c] + xc[c + 1]);
+      else if (!(i & 1) && (j & 1)) v = (T)0.5 * (xc[c] + xc[c + CW]);
+      else v = (T)0.5 * (xc[c] + xc[c + CW + 1]);
+      xs[q] += v;
     }
   __syncthreads();
   for (int s = 0; s < 2 * NU; ++s) {
-    tile_half_sweep<T, KK>(G, g, xs, fs, uk, RW, rx0, ry0, s + 1, RW - 2 - s, 1 - (s & 1), omega);
+    tile_half_sweep<T, KK>(G, g, xs, fs, uk, OX, OY, rx0, ry0, s + 1, RW - 2 - s, 1 - (s & 1), omega);
     __syncthreads();
   }
   for (int bb = threadIdx.y; bb < FT; bb += blockDim.y)
     for (int aa = threadIdx.x; aa < FT; aa += blockDim.x) {
-      const int i = t.x0 + aa, j = t.y0 + bb, q = (bb + HALO) * RW + aa + HALO;
+      const int i = t.x0 + aa, j = t.y0 + bb, q = (bb + MLEV_TMA_FOY) * SW + aa + MLEV_TMA_FOX;
       if (i <= g.nx && j <= g.ny && uk[q]) X[g.off + (long long)j * g.pitch + i] = xs[q];
     }
 }
@@ -228,11 +326,16 @@ __device__ void tail_direct(const SmGrid<T>& s, const T* __restrict__ inv, T* fb
     fbuf[r] = s.m[q] ? s.f[q] : (T)0;
   }
   __syncthreads();
-  for (int r = tid; r < nd; r += nt) {
-    const int j = r / nx1 + 1, i = r - (j - 1) * nx1 + 1, q = j * s.W + i;
+  // one warp per row of the inverse: coalesced loads, shuffle reduction
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int r = warp; r < nd; r += nw) {
     T acc = (T)0;
-    for (int c = 0; c < nd; ++c) acc += inv[r * nd + c] * fbuf[c];
-    s.x[q] = s.m[q] ? acc : (T)0;
+    for (int c = lane; c < nd; c += 32) acc += inv[r * nd + c] * fbuf[c];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const int j = r / nx1 + 1, i = r - (j - 1) * nx1 + 1, q = j * s.W + i;
+      s.x[q] = s.m[q] ? acc : (T)0;
+    }
   }
   __syncthreads();
 }
@@ -336,13 +439,11 @@ __global__ void __launch_bounds__(512) k_mg_tail(DevGeom G, const Tile* __restri
 
 template <typename T, int NU>
 size_t down_smem() {
-  constexpr int RW = FT + 2 * (2 * NU + 2);
-  return (size_t)RW * RW * (2 * sizeof(T) + 1);
+  return FusedSmem<T>::total + 128;  // + room to align the base to 128 bytes
 }
 template <typename T, int NU>
 size_t up_smem() {
-  constexpr int RW = FT + 2 * (2 * NU);
-  return (size_t)RW * RW * (2 * sizeof(T) + 1);
+  return FusedSmem<T>::total + 128;
 }
 
 template <typename T, int KK, int NU>

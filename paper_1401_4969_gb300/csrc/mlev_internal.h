@@ -26,7 +26,22 @@ struct GridDesc {
   long long roff;    // byte offset of the region grid in the region pool
   long long off;     // element offset of node (0,0) in the X / F pools
   long long off64;   // element offset in the FP64 pools (finest grid only, else -1)
+  int tmap;          // first of this grid's 3 TMA tensor maps (x fine box, f fine box, x coarse box), -1 if none
+  int pad_;
 };
+
+// TMA boxes of the fused multigrid kernels (nodes): the fine box covers a 64 x 64 output
+// tile with a halo of up to 8 columns and 6 rows; the coarse box covers the coarse nodes
+// the prolongation of such a tile (halo <= 4) reads.
+#define MLEV_TMA_FBW 80
+#define MLEV_TMA_FBH 76
+#define MLEV_TMA_FOX 8   // fine box starts at (x0 - 8, y0 - 6)
+#define MLEV_TMA_FOY 6
+#define MLEV_TMA_CBW 40
+#define MLEV_TMA_CBH 38
+#define MLEV_TMA_COX 4   // coarse box starts at (x0/2 - 4, y0/2 - 3)
+#define MLEV_TMA_COY 3
+#define MLEV_TMAP_BYTES 128
 
 struct Tile {  // a block of nodes of one grid: origin (x0, y0), size fixed by the kernel
   int grid;
@@ -50,6 +65,8 @@ struct DevGeom {
   const int16_t* qlabel;    // [4*ncy][4*ncx]: -1 outside Omega, 0 strip, j+1 inside G_j
   const uint8_t* cell_in;   // [ncy][ncx]
   const int* sub_top;       // [B*m] grid index of the finest grid of subdomain j of problem b (current level)
+  const unsigned char* tmaps;  // TMA tensor maps, MLEV_TMAP_BYTES each (64-byte aligned)
+  unsigned long long* status;  // device status bits (MLEV_ST_*), problem 0's flags slot
   int ncx, ncy, m;
   double H;
   KappaDev kap;
@@ -68,6 +85,7 @@ struct GlobalLayout {
 #define MLEV_ST_RR_NOCONV 2
 #define MLEV_ST_RR_BREAKDOWN 4
 #define MLEV_ST_NONFINITE 8
+#define MLEV_ST_TIMEOUT 16  // a bounded wait on a TMA transaction barrier gave up
 
 // Per-problem status record (long long slots), stride mlev_stat_stride(n).
 #define MLEV_STAT_L1_IT 0     // level-1 iterations

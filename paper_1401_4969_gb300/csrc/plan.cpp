@@ -232,6 +232,7 @@ std::string Plan::build(const mlev_opts& o) {
   for (auto c : cell_in) dom_full = dom_full && c;
 
   // ---- grids and tiles ----
+  n_tmap_grids = 0;
   grids.clear();
   tiles.clear();
   sub_top.clear();
@@ -279,6 +280,7 @@ std::string Plan::build(const mlev_opts& o) {
           g.off = pool;
           pool += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
           g.off64 = -1;
+          g.tmap = -1;
           if (dpt == 0) {
             g.off64 = pool64;
             pool64 += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
@@ -313,6 +315,7 @@ std::string Plan::build(const mlev_opts& o) {
         g.off = pool;
         pool += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
         g.off64 = -1;
+        g.tmap = -1;
         if (dpt == 0) {
           g.off64 = pool64;
           pool64 += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
@@ -402,6 +405,14 @@ std::string Plan::build(const mlev_opts& o) {
     };
     plan_fused(sub_by_depth, P.sub_f, P.sub_dt, P.sub_tail, P.sub_tail_smem, sub_direct ? nd_max : 0);
     plan_fused(strip_by_depth, P.strip_f, P.strip_dt, P.strip_tail, P.strip_tail_smem, 0);
+    // TMA tensor maps for every grid a fused down / up kernel reads (depths 0 .. dt)
+    auto give_maps = [&](const std::vector<std::vector<int>>& by_depth, int dt) {
+      if (dt == 0) return;
+      for (int d = 0; d <= std::min(dt, (int)by_depth.size() - 1); ++d)
+        for (int gi : by_depth[d]) grids[gi].tmap = 3 * n_tmap_grids++;
+    };
+    give_maps(sub_by_depth, P.sub_dt);
+    give_maps(strip_by_depth, P.strip_dt);
     P.pool_elems = pool;
     P.pool64_elems = pool64;
     // unknown counts per problem (reports and the traffic model)
@@ -443,6 +454,7 @@ std::string Plan::build(const mlev_opts& o) {
       g.off = l1pool;
       l1pool += round_up((long long)(g.ny + 1) * g.pitch, kAlignElems);
       g.off64 = -1;
+      g.tmap = -1;
       grids.push_back(g);
     }
   l1_pool_elems = l1pool;
@@ -460,6 +472,7 @@ std::string Plan::build(const mlev_opts& o) {
   take(w_qlabel, qlabel.size() * sizeof(int16_t));
   take(w_cellin, cell_in.size());
   take(w_subtop, std::max<size_t>(1, sub_top.size()) * sizeof(int));
+  take(w_tmaps, std::max<size_t>(1, (size_t)3 * n_tmap_grids) * MLEV_TMAP_BYTES);
   tables_bytes = cur;
   // coefficient staging and per-level triangle values
   size_t kst = 0;

@@ -85,12 +85,13 @@ struct Plan {
   int sub_direct = 0;                      // subdomain coarsest grids solved by a dense inverse
   int nd_max = 0;                          // largest coarsest-window size (interior nodes) of a subdomain
   int strip_coarse_nodes = 0;              // nodes of the strip's coarsest (T_{h_2}) grid
+  int n_tmap_grids = 0;                    // grids carrying TMA tensor maps (3 maps each)
 
   // ---- workspace layout (depends on opts) ----
   int tsize = 4;
   Span w_grids, w_tiles, w_regions, w_qlabel, w_cellin, w_subtop;
   Span w_kstage, w_klvl, w_band, w_ut[2], w_uin, w_r, w_l1vec, w_l1pool[2];
-  Span w_x, w_f, w_x64, w_aug, w_lam, w_c, w_c0, w_stat, w_jobnorm, w_chol, w_out_lam, w_out_u, w_cinv;
+  Span w_x, w_f, w_x64, w_aug, w_lam, w_c, w_c0, w_stat, w_jobnorm, w_chol, w_out_lam, w_out_u, w_cinv, w_tmaps;
   size_t ws_bytes = 0;
   size_t tables_bytes = 0;
   KappaDev kap_template{};  // offsets relative to the workspace base
