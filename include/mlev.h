@@ -216,6 +216,40 @@ int mlev_solve_noalloc(mlev_ctx* ctx, const mlev_opts* opts, void* stream, doubl
  */
 int mlev_profile_read(mlev_ctx* ctx, mlev_kernel_stat* out, int capacity, int* count);
 
+/*
+ * Derivative of the final eigenvalue lambda_{h_n} of Algorithm 4.2 (with the correction
+ * step of Algorithm 4.1) with respect to the coefficient kappa of a(u, v) = int kappa
+ * grad u . grad v (Section 2.2), by the adjoint (reverse) method.
+ *
+ * The map differentiated is the algorithm itself, every local and G_{m+1} solve
+ * (Eqs. Aux_Problem, G_m+1_Problem) and both eigenproblems (Algorithm 4.2 step 1,
+ * Eq. Eigen_Augment_Problem) taken as exact; the discrete solves use the same
+ * multigrid, precision and cycle counts as mlev_solve with the same opts. The call
+ * runs the forward solve again (keeping u~_k, lambda_k and the Rayleigh-Ritz
+ * coefficients of every level), then the reverse sweep, in which the local solutions
+ * e^j of each level are recomputed rather than stored.
+ *
+ *   dlambda   [batch] device: upstream weights w_b; the result is w_b * dlambda_b/dkappa
+ *   layout    MLEV_GRAD_FINE_ELEM: dkappa[b][cj][ci][t] per triangle of T_{h_n}
+ *             (t = 0 lower, 1 upper; the derivative with respect to a coefficient given
+ *             per finest triangle, whatever kappa_kind is);
+ *             MLEV_GRAD_COARSE_CELL: dkappa[b][cj][ci] per T_H cell (a coefficient
+ *             constant on each coarse cell)
+ *   dkappa    device output, overwritten; zero outside Omega
+ *   lambda_out  nullable [batch] device: lambda_{h_n} of the forward pass
+ *   rep         nullable host report, as in mlev_solve
+ *
+ * The workspace must hold mlev_grad_workspace_size bytes (more than mlev_solve's: level
+ * checkpoints and adjoint fields). Errors as in mlev_solve; MLEV_ENOCONV also when the
+ * level-1 adjoint solve reaches its cap (4 * level1_max_iter iterations). Not captured
+ * in a CUDA graph (opts.use_graph is ignored); opts.profile times its launches.
+ */
+#define MLEV_GRAD_FINE_ELEM 0
+#define MLEV_GRAD_COARSE_CELL 1
+int mlev_grad_workspace_size(mlev_ctx* ctx, const mlev_opts* opts, size_t* bytes);
+int mlev_grad_kappa(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
+                    const double* dlambda, int layout, double* dkappa, double* lambda_out, mlev_report* rep);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,13 +94,15 @@ P* at(void* base, const Span& s) {
 // Kernel families for profiling (names reported by mlev_profile_read).
 enum Fam {
   F_KAPPA, F_BAND, F_LEVEL1, F_INTERP, F_RHS, F_GATHER, F_SMOOTH, F_RESTRICT, F_PROLONG, F_COARSEST, F_ACCUM,
-  F_REFINE, F_GLUE, F_STRIP_RHS, F_STRIP_UPD, F_AUG, F_RR, F_OUT, F_RESNORM, F_MG_DOWN, F_MG_UP, F_MG_TAIL, F_COUNT
+  F_REFINE, F_GLUE, F_STRIP_RHS, F_STRIP_UPD, F_AUG, F_RR, F_OUT, F_RESNORM, F_MG_DOWN, F_MG_UP, F_MG_TAIL,
+  F_ADJ_RR, F_ADJ_FIELD, F_ADJ_GRAD, F_ADJ_LEVEL1, F_COUNT
 };
 const char* kFamName[F_COUNT] = {"kappa_levels", "coarse_band", "level1_lobpcg", "interp_embed", "rhs_aux",
                                  "mg_gather", "mg_smooth", "mg_restrict", "mg_prolong", "mg_coarsest",
                                  "mixed_accumulate", "mixed_refine_residual", "glue", "strip_rhs", "strip_update",
                                  "aug_inner", "rayleigh_ritz", "output", "residual_check", "mg_down_fused",
-                                 "mg_up_fused", "mg_tail"};
+                                 "mg_up_fused", "mg_tail", "adj_rayleigh_ritz", "adj_fields",
+                                 "adj_element_grad", "adj_level1"};
 
 struct ProfRec {
   int fam;
@@ -121,6 +123,11 @@ struct Launcher {
   std::vector<ProfRec>* recs = nullptr;
   std::vector<cudaEvent_t>* pool = nullptr;
   size_t next_ev = 0;
+  // level checkpoints kept by the forward pass of mlev_grad_kappa (null: plain solve):
+  // u~_k of level k at ck_ut + (k-1) B bstride, coefficients of u_{h_k} at ck_c + k B ncoef
+  double* ck_ut = nullptr;
+  double* ck_c = nullptr;
+  double* ck_c0 = nullptr;
 
   const Tile* tiles_at(const TileList& t) const { return at<Tile>(ws, P.w_tiles) + t.off; }
 
@@ -232,7 +239,7 @@ struct Launcher {
   template <typename T>
   void solve_set(const std::vector<TileList>& lists, const TileList& coarsest, int vcycles, T* X, T* F, double* X64,
                  const double* R, int cmode, const std::vector<TileList>* fl = nullptr, int dt = 0,
-                 const TileList* tail = nullptr, size_t tail_smem = 0) {
+                 const TileList* tail = nullptr, size_t tail_smem = 0, bool rmask = false) {
     const int D = (int)lists.size() - 1;
     const bool fused = o.fused && fl && tail && dt <= D && o.pre_smooth >= 1 && o.pre_smooth <= 2 &&
                        o.post_smooth >= 1 && o.post_smooth <= 2;
@@ -244,8 +251,12 @@ struct Launcher {
     for (int pass = 0; pass < passes; ++pass) {
       if (pass > 0) {
         go(F_ACCUM, (2 * t + 16) * top.unk, [&] { launch_accumulate<T>(G, tiles_at(top), top.count, X, X64, s); });
-        go(F_REFINE, (16 + t + kfine_extra()) * top.unk,
-           [&] { launch_refine_residual<T>(G, P.glay, tiles_at(top), top.count, F, X64, R, s); });
+        go(F_REFINE, (16 + t + kfine_extra()) * top.unk, [&] {
+          if (rmask)  // subdomain j's right-hand side is R on closed G_j only (adjoint solves)
+            launch_refine_residual_masked<T>(G, P.glay, tiles_at(top), top.count, F, X64, R, s);
+          else
+            launch_refine_residual<T>(G, P.glay, tiles_at(top), top.count, F, X64, R, s);
+        });
       }
       for (int v = 0; v < cyc; ++v) {
         if (fused)
@@ -314,6 +325,10 @@ struct Launcher {
     double* lam = at<double>(ws, P.w_lam);
     double* c = at<double>(ws, P.w_c);
     double* c0 = at<double>(ws, P.w_c0);
+    const size_t ncoef = (size_t)(P.ncx + 1) * (P.ncy + 1);
+    auto utL = [&](int l) { return ck_ut ? ck_ut + (size_t)(l - 1) * B * P.glay.bstride : ut[l & 1]; };
+    auto cL = [&](int l) { return ck_c ? ck_c + (size_t)l * B * ncoef : c; };
+    auto c0L = [&](int l) { return ck_c0 ? ck_c0 + (size_t)l * B : c0; };
     // ---- Algorithm 4.2 step 1: eigenproblem on V_{0h_1}
     {
       Level1Args a{};
@@ -330,11 +345,11 @@ struct Launcher {
       a.omega = o.omega;
       a.max_iter = o.level1_max_iter;
       a.tol = o.level1_tol;
-      a.ut1 = ut[1];
+      a.ut1 = utL(1);
       a.lam = lam;
       a.lam_stride = n + 1;
-      a.c = c;
-      a.c0 = c0;
+      a.c = cL(1);
+      a.c0 = c0L(1);
       a.stat = stat;
       a.stat_stride = stat_stride;
       go(F_LEVEL1, 0.0, [&] { launch_level1<T>(G, P.glay, a, s); });
@@ -351,12 +366,12 @@ struct Launcher {
       LevelArgs a{};
       a.L = L;
       a.B = B;
-      a.ut_prev = ut[(L - 1) & 1];
-      a.ut = ut[L & 1];
+      a.ut_prev = utL(L - 1);
+      a.ut = utL(L);
       a.uin = uin;
       a.r = r;
-      a.c = c;
-      a.c0 = c0;
+      a.c = cL(L - 1);
+      a.c0 = c0L(L - 1);
       a.lam = lam;
       a.lam_stride = n + 1;
       go(F_INTERP, 10.0 * nfree, [&] { launch_interp(G, P.glay, a, s); });
@@ -409,8 +424,8 @@ struct Launcher {
       rr.chol = at<double>(ws, P.w_chol);
       rr.partials = partials;
       rr.lam = lam;
-      rr.c = c;
-      rr.c0 = c0;
+      rr.c = cL(L);
+      rr.c0 = c0L(L);
       rr.stat = stat;
       rr.stat_stride = stat_stride;
       rr.max_iter = o.rr_max_iter;
@@ -420,9 +435,182 @@ struct Launcher {
     go(F_OUT, 16.0 * B, [&] { launch_lambda_out(B, n, lam, lambda_out, s); });
     if (u_out)
       go(F_OUT, 16.0 * B * (P.lvl_nx(n) + 1) * (P.lvl_ny(n) + 1),
-         [&] { launch_output_u(G, P.glay, n, B, ut[n & 1], c, c0, u_out, s); });
+         [&] { launch_output_u(G, P.glay, n, B, utL(n), cL(n), c0L(n), u_out, s); });
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    return MLEV_OK;
+  }
+
+  // Forward pass with level checkpoints, then the reverse sweep of Algorithm 4.2 for
+  // dlambda_{h_n}/dkappa (kernels and the derivation: kern_adj.cu).
+  template <typename T>
+  int run_grad(const double* dl, int layout, double* dkappa, double* lambda_out) {
+    const int B = P.B, n = P.n;
+    const bool mixed = sizeof(T) == 4;
+    const double t = sizeof(T);
+    const int ncoef = (P.ncx + 1) * (P.ncy + 1);
+    const size_t gfield = (size_t)B * P.glay.bstride;
+    ck_ut = at<double>(ws, P.g_ck_ut);
+    ck_c = at<double>(ws, P.g_ck_c);
+    ck_c0 = at<double>(ws, P.g_ck_c0);
+    int rc = run<T>(lambda_out ? lambda_out : at<double>(ws, P.w_out_lam), nullptr);
+    if (rc) return rc;
+    double* lam = at<double>(ws, P.w_lam);
+    double* lambar = at<double>(ws, P.g_lambar);
+    double* ubar[2] = {at<double>(ws, P.g_ubar[0]), at<double>(ws, P.g_ubar[1])};
+    double* utbar = at<double>(ws, P.g_utbar);
+    double* sbar = at<double>(ws, P.g_sbar);
+    double* rbar = at<double>(ws, P.g_rbar);
+    double* tbuf = at<double>(ws, P.g_tbuf);
+    double* glb = at<double>(ws, P.g_gl);
+    double* coef = at<double>(ws, P.g_coef);
+    double* part2 = at<double>(ws, P.g_part2);
+    double* lbpart = at<double>(ws, P.g_lbpart);
+    double* uin = at<double>(ws, P.w_uin);
+    double* r = at<double>(ws, P.w_r);
+    double* partials = at<double>(ws, P.w_aug);
+    double* KH = at<double>(ws, P.w_band);
+    double* MH = KH + (size_t)B * P.nhb * (P.bw + 1);
+    long long* stat = at<long long>(ws, P.w_stat);
+    const int stat_stride = mlev_stat_stride(n);
+    const int cstride = 3 * ncoef + kAdjScal;
+    T* X = at<T>(ws, P.w_x);
+    T* F = at<T>(ws, P.w_f);
+    double* X64 = mixed ? at<double>(ws, P.w_x64) : nullptr;
+    const double* E = mixed ? X64 : reinterpret_cast<const double*>(X);
+    const int use64 = mixed ? 1 : 0;
+    const int sub_cmode = P.sub_direct ? C_DIRECT : C_SWEEPS;
+    const int strip_cmode =
+        coarsest_smem_bytes(P.kappa_kind, P.strip_coarse_nodes, sizeof(T)) <= 220 * 1024 ? C_SMEM : C_SWEEPS;
+    cudaMemsetAsync(glb, 0, P.g_gl.bytes, s);
+    cudaMemsetAsync(ubar[n & 1], 0, gfield * 8, s);
+    go(F_ADJ_FIELD, 0.0, [&] { launch_lambar_init(B, n, dl, lambar, s); });
+    for (int L = n; L >= 2; --L) {
+      const int k = L - 1;
+      const LevelPlan& lp = P.lp[L];
+      const double nfree = (double)lp.n_free * B;
+      G.sub_top = at<int>(ws, P.w_subtop) + lp.sub_top_off;
+      double* gL = glb + P.gl_off[L];
+      double* ubL = ubar[L & 1];
+      double* utl = ck_ut + (size_t)(L - 1) * gfield;
+      LevelArgs a{};
+      a.L = L;
+      a.B = B;
+      a.ut_prev = ck_ut + (size_t)(k - 1) * gfield;
+      a.ut = utl;
+      a.uin = uin;
+      a.r = r;
+      a.c = ck_c + (size_t)k * B * ncoef;
+      a.c0 = ck_c0 + (size_t)k * B;
+      a.lam = lam;
+      a.lam_stride = n + 1;
+      // u_in and r of the forward level (cheap to recompute), inner products of u~_L
+      go(F_INTERP, 10.0 * nfree, [&] { launch_interp(G, P.glay, a, s); });
+      go(F_RHS, (16.0 + kfine_extra()) * nfree, [&] { launch_rhs(G, P.glay, a, s); });
+      go(F_AUG, (8.0 + kfine_extra()) * nfree, [&] { launch_aug(G, P.glay, a, partials, s); });
+      // Rayleigh-Ritz adjoint
+      go(F_ADJ_FIELD, 16.0 * nfree, [&] { launch_cbar(G, P.glay, L, B, utl, ubL, part2, s); });
+      RRAdjArgs ra{};
+      ra.B = B;
+      ra.L = L;
+      ra.n = n;
+      ra.nhb = P.nhb;
+      ra.bw = P.bw;
+      ra.KH = KH;
+      ra.MH = MH;
+      ra.scratch = at<double>(ws, P.g_rrscr);
+      ra.smem = rr_adj_smem_bytes(P.nhb, P.bw) <= (size_t)kRRSmemMax;
+      ra.partials = partials;
+      ra.part2 = part2;
+      ra.lam = lam;
+      ra.lambar = lambar;
+      ra.c = ck_c + (size_t)L * B * ncoef;
+      ra.c0 = ck_c0 + (size_t)L * B;
+      ra.coef = coef;
+      ra.cstride = cstride;
+      ra.stat = stat;
+      ra.stat_stride = stat_stride;
+      go(F_ADJ_RR, 0.0, [&] { launch_rr_adj(G, ra, s); });
+      go(F_ADJ_FIELD, 32.0 * nfree, [&] { launch_adj_ut(G, P.glay, L, B, utl, ubL, coef, cstride, utbar, s); });
+      const AugField fu{ck_c + (size_t)L * B * ncoef, ncoef, ck_c0 + (size_t)L * B, 1, utl};
+      const AugField fz{coef, cstride, coef + 3 * ncoef + ADJ_ZU, cstride, utl};
+      go(F_ADJ_GRAD, 24.0 * nfree, [&] { launch_grad_aug(G, P.glay, L, B, fu, fz, lambar + L, n + 1, -1.0, gL, s); });
+      // G_{m+1} adjoint: K_SS sbar = utbar on the strip
+      cudaMemsetAsync(sbar, 0, gfield * 8, s);
+      const TileList& stop = lp.strip[0];
+      if (stop.count) {
+        cudaMemsetAsync(X, 0, (size_t)lp.pool_elems * sizeof(T), s);
+        go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * stop.unk,
+           [&] { launch_gather<T>(G, P.glay, tiles_at(stop), stop.count, X, F, X64, utbar, s); });
+        solve_set<T>(lp.strip, lp.strip_coarsest, o.strip_vcycles, X, F, X64, utbar, strip_cmode, &lp.strip_f,
+                     lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem);
+        LevelArgs as = a;
+        as.ut = sbar;
+        go(F_STRIP_UPD, 24.0 * stop.unk,
+           [&] { launch_strip_update(G, P.glay, as, tiles_at(stop), stop.count, E, use64, s); });
+        go(F_ADJ_FIELD, 24.0 * nfree, [&] { launch_strip_adj_post(G, P.glay, L, B, utbar, sbar, s); });
+        go(F_ADJ_GRAD, 16.0 * nfree, [&] { launch_grad_pair(G, P.glay, L, B, -1.0, sbar, utl, gL, s); });
+      }
+      // local adjoints t_j = A_j^{-1} (utbar on closed G_j), kept aside
+      const TileList& top = lp.sub[0];
+      cudaMemsetAsync(X, 0, (size_t)lp.pool_elems * sizeof(T), s);
+      go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * top.unk,
+         [&] { launch_gather_masked<T>(G, P.glay, tiles_at(top), top.count, X, F, X64, utbar, s); });
+      solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, utbar, sub_cmode, &lp.sub_f, lp.sub_dt,
+                   &lp.sub_tail, lp.sub_tail_smem, true);
+      const size_t ebytes = (size_t)(mixed ? lp.pool64_elems : lp.pool_elems) * 8;
+      cudaMemcpyAsync(tbuf, E, ebytes, cudaMemcpyDeviceToDevice, s);
+      // the forward local solutions e^j, recomputed
+      cudaMemsetAsync(X, 0, (size_t)lp.pool_elems * sizeof(T), s);
+      go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * top.unk,
+         [&] { launch_gather<T>(G, P.glay, tiles_at(top), top.count, X, F, X64, r, s); });
+      solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, r, sub_cmode, &lp.sub_f, lp.sub_dt, &lp.sub_tail,
+                   lp.sub_tail_smem);
+      go(F_ADJ_GRAD, 32.0 * top.unk, [&] { launch_grad_local(G, P.glay, L, B, tbuf, E, use64, uin, gL, s); });
+      go(F_ADJ_FIELD, 8.0 * top.unk + 8.0 * nfree, [&] { launch_rbar(G, P.glay, L, B, tbuf, use64, rbar, s); });
+      const int nblk = adj_uin_blocks(P.glay, L);
+      go(F_ADJ_FIELD, 40.0 * nfree, [&] {
+        launch_adj_uin(G, P.glay, L, B, utbar, sbar, rbar, uin, lam, n + 1, lbpart, P.adj_nblk, s);
+      });
+      go(F_ADJ_FIELD, 8.0 * nblk * B,
+         [&] { launch_lambar_finalize(B, nblk, P.adj_nblk, lbpart, lambar, n + 1, k, s); });
+      go(F_ADJ_FIELD, 16.0 * nfree, [&] { launch_restrict_adj(G, P.glay, k, B, utbar, ubar[k & 1], s); });
+    }
+    // level 1: eigenvector adjoint, then its element terms
+    {
+      Level1AdjArgs la{};
+      la.B = B;
+      la.grid_begin = P.l1_grid_begin;
+      la.nlev = P.l1_nlev;
+      la.vec = at<double>(ws, P.w_l1vec);
+      la.vstride = P.w_l1vec.bytes / 8 / 10 / B;
+      la.xpool = at<void>(ws, P.w_l1pool[0]);
+      la.fpool = at<void>(ws, P.w_l1pool[1]);
+      la.pre = o.pre_smooth;
+      la.post = o.post_smooth;
+      la.coarse_sweeps = std::max(4, o.coarse_sweeps / 4);
+      la.omega = o.omega;
+      la.max_iter = 4 * o.level1_max_iter;
+      la.tol = 1e-11;
+      la.ut1 = ck_ut;
+      la.ubar1 = ubar[1];
+      la.lam = lam;
+      la.lam_stride = n + 1;
+      la.zout = sbar;
+      la.stat = stat;
+      la.stat_stride = stat_stride;
+      go(F_ADJ_LEVEL1, 0.0, [&] { launch_level1_adj<T>(G, P.glay, la, s); });
+      const AugField f1{nullptr, 0, nullptr, 0, ck_ut}, f2{nullptr, 0, nullptr, 0, sbar};
+      go(F_ADJ_GRAD, 24.0 * B * P.lvl_nx(1) * P.lvl_ny(1),
+         [&] { launch_grad_aug(G, P.glay, 1, B, f1, f2, lambar + 1, n + 1, -1.0, glb + P.gl_off[1], s); });
+    }
+    GradLevels gv{};
+    for (int l = 1; l <= n; ++l) gv.off[l] = P.gl_off[l];
+    go(F_ADJ_GRAD, 16.0 * B * P.lvl_nx(n) * P.lvl_ny(n) * 2,
+       [&] { launch_grad_spread(G, P.glay, n, B, gv, glb, layout, dkappa, s); });
+    ck_ut = ck_c = ck_c0 = nullptr;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch (adjoint)");
     return MLEV_OK;
   }
 };
@@ -565,7 +753,7 @@ int fill_report(mlev_ctx* ctx, void* ws, cudaStream_t s, mlev_report* rep) {
   rep->d2h_bytes = ctx->io_d2h;
   if (flags & MLEV_ST_TIMEOUT)
     return fail(ctx, MLEV_ETIMEOUT, "a bounded device-side wait gave up (status flags " + std::to_string(flags) + ")");
-  if (flags & (MLEV_ST_LEVEL1_NOCONV | MLEV_ST_RR_NOCONV))
+  if (flags & (MLEV_ST_LEVEL1_NOCONV | MLEV_ST_RR_NOCONV | MLEV_ST_ADJ_NOCONV))
     return fail(ctx, MLEV_ENOCONV, "an iteration reached its cap (status flags " + std::to_string(flags) + ")");
   if (flags) return fail(ctx, MLEV_ENOCONV, "numerical breakdown (status flags " + std::to_string(flags) + ")");
   return MLEV_OK;
@@ -630,6 +818,36 @@ int solve_impl(mlev_ctx* ctx, const mlev_opts* o, void* ws, size_t ws_bytes, cud
   rc = o->precision == MLEV_PREC_FP64 ? ln.run<double>(lambda_out, u_out) : ln.run<float>(lambda_out, u_out);
   ctx->launches = ln.count;
   return rc;
+}
+
+int grad_impl(mlev_ctx* ctx, const mlev_opts* o, void* ws, cudaStream_t s, const double* kappa_src,
+              const double* dl, int layout, double* dkappa, double* lambda_out) {
+  const Plan& P = ctx->plan;
+  Launcher ln{ctx, P, *o, ws, s};
+  ln.kappa_src = kappa_src;
+  std::vector<ProfRec> recs;
+  if (o->profile) {
+    ln.profiling = true;
+    ln.recs = &recs;
+    ln.pool = &ctx->ev_pool;
+  }
+  int rc = o->precision == MLEV_PREC_FP64 ? ln.run_grad<double>(dl, layout, dkappa, lambda_out)
+                                          : ln.run_grad<float>(dl, layout, dkappa, lambda_out);
+  ctx->launches = ln.count;
+  if (rc) return rc;
+  if (o->profile) {
+    CK(cudaStreamSynchronize(s));
+    ctx->prof.assign(F_COUNT, ProfRecHost());
+    for (const ProfRec& r : recs) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, r.a, r.b));
+      ctx->prof[r.fam].launches++;
+      ctx->prof[r.fam].ms += ms;
+      ctx->prof[r.fam].bytes += r.bytes;
+    }
+    ctx->prof_valid = true;
+  }
+  return MLEV_OK;
 }
 
 const double* kappa_device_src(mlev_ctx* ctx, void* ws) {
@@ -845,6 +1063,36 @@ int mlev_solve_host(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_
     ctx->io_d2h += (long long)ub;
   }
   CK(cudaStreamSynchronize(s));
+  if (rep) return fill_report(ctx, workspace, s, rep);
+  return MLEV_OK;
+}
+
+int mlev_grad_workspace_size(mlev_ctx* ctx, const mlev_opts* opts, size_t* bytes) {
+  if (!ctx || !bytes) return MLEV_EINVAL;
+  if (!opts_valid(opts)) return fail(ctx, MLEV_EINVAL, "invalid options");
+  int rc = ensure_plan(ctx, opts);
+  if (rc) return rc;
+  *bytes = ctx->plan.ws_grad_bytes;
+  return MLEV_OK;
+}
+
+int mlev_grad_kappa(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
+                    const double* dlambda, int layout, double* dkappa, double* lambda_out, mlev_report* rep) {
+  int rc = prepare(ctx, opts, workspace, ws_bytes);
+  if (rc) return rc;
+  const Plan& P = ctx->plan;
+  if (ws_bytes < P.ws_grad_bytes)
+    return fail(ctx, MLEV_ENOMEM, "workspace too small for the adjoint: need " + std::to_string(P.ws_grad_bytes) +
+                                      " bytes (mlev_grad_workspace_size)");
+  if (!dlambda || !dkappa) return fail(ctx, MLEV_EINVAL, "dlambda and dkappa are required");
+  if (layout != MLEV_GRAD_FINE_ELEM && layout != MLEV_GRAD_COARSE_CELL)
+    return fail(ctx, MLEV_EINVAL, "unknown gradient layout");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, MLEV_ECUDA, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = upload_tables(ctx, workspace, s, false);
+  if (rc) return rc;
+  rc = grad_impl(ctx, opts, workspace, s, kappa_device_src(ctx, workspace), dlambda, layout, dkappa, lambda_out);
+  if (rc) return rc;
   if (rep) return fill_report(ctx, workspace, s, rep);
   return MLEV_OK;
 }

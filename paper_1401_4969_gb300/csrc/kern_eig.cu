@@ -16,6 +16,7 @@
 //   unique root; it is found by Newton's method safeguarded by bisection, with a
 //   banded Cholesky factorisation of S(mu) per step. The eigenvector is
 //   c = [-S(mu)^{-1} w ; 1], scaled to b(u,u) = 1 and int u > 0.
+#include "kern_band.cuh"
 #include "kern_blk.cuh"
 #include "kern_launch.h"
 
@@ -286,58 +287,6 @@ template void launch_level1<float>(const DevGeom&, const GlobalLayout&, const Le
 template void launch_level1<double>(const DevGeom&, const GlobalLayout&, const Level1Args&, cudaStream_t);
 
 // ---------------------------------------------------------------- Rayleigh-Ritz
-// Band LDL^T factorisation of S = K_H - mu M_H (row-major band [r][d] = S(r, r-d)) with
-// the right-hand side eliminated alongside (forward substitution of L z = w), one block
-// barrier per column. On return Lb holds the unscaled columns (L(i,j) = Lb[i][i-j] / D_j),
-// invD[j] = 1 / D_j and y = z. Returns false (to all threads) if a pivot is not positive,
-// i.e. mu is not below the smallest eigenvalue of (K_H, M_H).
-__device__ bool band_ldlt(double* Lb, double* invD, double* y, const int* pairs, int npair, int N, int bw,
-                          int* flag) {
-  const int bw1 = bw + 1;
-  if (threadIdx.x == 0) *flag = 1;
-  __syncthreads();
-  for (int j = 0; j < N; ++j) {
-    const double Dj = Lb[(long long)j * bw1];
-    if (!(Dj > 0.0)) {  // identical decision in every thread
-      if (threadIdx.x == 0) *flag = 0;
-      return false;
-    }
-    const double inv = 1.0 / Dj;
-    const int last = min(N - 1, j + bw);
-    const double yj = y[j];
-    for (int q = threadIdx.x; q < npair + bw; q += blockDim.x) {
-      if (q < npair) {
-        const int aa = pairs[q] >> 16, bb = pairs[q] & 0xffff;
-        const int i = j + 1 + aa, k = j + 1 + bb;
-        if (i <= last)
-          Lb[(long long)i * bw1 + (i - k)] -= Lb[(long long)i * bw1 + (i - j)] * Lb[(long long)k * bw1 + (k - j)] * inv;
-      } else {
-        const int i = j + 1 + (q - npair);
-        if (i <= last) y[i] -= Lb[(long long)i * bw1 + (i - j)] * inv * yj;
-      }
-    }
-    if (threadIdx.x == 0) invD[j] = inv;
-    __syncthreads();
-  }
-  return true;
-}
-
-// Back substitution L^T x = D^{-1} z in place (x overwrites y), warp 0, column-oriented.
-__device__ void band_back(const double* Lb, const double* invD, double* y, int N, int bw) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x, bw1 = bw + 1;
-    for (int i = N - 1; i >= 0; --i) {
-      const double xi = y[i] * invD[i];
-      __syncwarp();
-      if (lane == 0) y[i] = xi;
-      // remove x_i from the rows above it: z[i-d] -= L(i, i-d) D_{i-d} x_i = Lb[i][d] x_i
-      for (int d = 1 + lane; d <= bw && i - d >= 0; d += 32) y[i - d] -= Lb[(long long)i * bw1 + d] * xi;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-}
-
 __global__ void __launch_bounds__(256) k_rr(DevGeom G, RRArgs a) {
   extern __shared__ double rr_sm[];
   __shared__ double scratch[8 * 4];

@@ -2,6 +2,7 @@
 // u_{h_k} into V_{h_{k+1}}, the right-hand side of the auxiliary problems, the
 // gluing of step 2, the G_{m+1} right-hand side, the inner products of step 3,
 // and set-up kernels for kappa and the coarse matrices.
+#include "kern_coarse.cuh"
 #include "kern_launch.h"
 
 namespace mlev {
@@ -9,19 +10,6 @@ namespace mlev {
 constexpr int GX = 32, GY = 8;
 
 __host__ __device__ __forceinline__ int lidx(int l) { return l - MLEV_LMIN; }
-
-// Value at global node (i, j) of level L of the coarse P1 function with nodal values
-// c[(ncy+1)(ncx+1)] (barycentric weights in the T_H triangle containing the node).
-__device__ __forceinline__ double coarse_eval(const DevGeom& G, const double* c, int L, int i, int j) {
-  const int ci = min(i >> L, G.ncx - 1), cj = min(j >> L, G.ncy - 1);
-  const int ri = i - (ci << L), rj = j - (cj << L);
-  const double S = (double)(1 << L);
-  const double s = ri / S, t = rj / S;
-  const int w = G.ncx + 1;
-  const double c00 = c[cj * w + ci], c11 = c[(cj + 1) * w + ci + 1];
-  if (ri >= rj) return c00 * (1.0 - s) + c[cj * w + ci + 1] * (s - t) + c11 * t;  // lower triangle
-  return c00 * (1.0 - t) + c11 * s + c[(cj + 1) * w + ci] * (t - s);              // upper triangle
-}
 
 // Exact embedding V_{h_{L-1}} -> V_{h_L} of a pitched level-(L-1) field at node (i, j).
 __device__ __forceinline__ double embed(const double* u, int pitch, int i, int j) {

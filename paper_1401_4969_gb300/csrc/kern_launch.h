@@ -122,4 +122,95 @@ void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s);
 size_t rr_smem_bytes(int nhb, int bw);
 constexpr int kRRSmemMax = 200 * 1024;
 
+// ---- adjoint of Algorithm 4.2 (kern_adj.cu) ----
+// A field of level L written as sum_i c_i phi_i^H + s * f (the basis {coarse hats, u~} of
+// the Rayleigh-Ritz step): c nullable ([B][ncoef], stride cstride), s nullable (read as 1),
+// f a global level-L field.
+struct AugField {
+  const double* c;
+  long long cstride;
+  const double* s;
+  int sstride;
+  const double* f;
+};
+struct GradLevels {                 // per-level triangle gradients [B][ny_l][nx_l][2]
+  long long off[MLEV_MAX_LEVELS + 1];  // element offset of level l (1..n)
+};
+// Per-problem coefficients the Rayleigh-Ritz adjoint hands to the field kernels:
+// [zc | kac | mac] coarse vectors (ncoef each) then kAdjScal scalars.
+constexpr int kAdjScal = 8;
+enum { ADJ_CU = 0, ADJ_ZU, ADJ_KAU, ADJ_MAU, ADJ_LAMBAR, ADJ_LAM, ADJ_SC, ADJ_SIGMA };
+struct RRAdjArgs {
+  int B, L, n;
+  int nhb, bw;
+  const double* KH;
+  const double* MH;
+  double* scratch;       // [B][nhb*(bw+1) + 10*nhb] (used when the system does not fit on chip)
+  int smem;
+  const double* partials;  // k_aug partials of u~_L
+  const double* part2;     // k_cbar partials of ubar
+  const double* lam;       // [B][n+1]
+  const double* lambar;    // [B][n+1]
+  const double* c;         // coefficients of u_L
+  const double* c0;
+  double* coef;            // [B][cstride]
+  int cstride;
+  long long* stat;
+  int stat_stride;
+};
+size_t rr_adj_smem_bytes(int nhb, int bw);
+struct Level1AdjArgs {
+  int B;
+  int grid_begin, nlev;
+  double* vec;
+  long long vstride;
+  void* xpool;
+  void* fpool;
+  int pre, post, coarse_sweeps;
+  double omega;
+  int max_iter;
+  double tol;
+  const double* ut1;     // u_{h_1}, global level-1 layout
+  const double* ubar1;   // its adjoint
+  const double* lam;     // [B][n+1]
+  int lam_stride;
+  double* zout;          // solution z, global level-1 layout
+  long long* stat;
+  int stat_stride;
+};
+template <typename T>
+void launch_gather_masked(const DevGeom& G, const GlobalLayout& gl, const Tile* tiles, int n, T* X, T* F, double* X64,
+                          const double* R, cudaStream_t s);
+template <typename T>
+void launch_refine_residual_masked(const DevGeom& G, const GlobalLayout& gl, const Tile* tiles, int n, T* F,
+                                   const double* X64, const double* R, cudaStream_t s);
+void launch_cbar(const DevGeom& G, const GlobalLayout& gl, int L, int B, const double* ut, const double* ubar,
+                 double* part2, cudaStream_t s);
+void launch_rr_adj(const DevGeom& G, const RRAdjArgs& a, cudaStream_t s);
+void launch_adj_ut(const DevGeom& G, const GlobalLayout& gl, int L, int B, const double* ut, const double* ubar,
+                   const double* coef, int cstride, double* utbar, cudaStream_t s);
+void launch_grad_aug(const DevGeom& G, const GlobalLayout& gl, int L, int B, const AugField& f1, const AugField& f2,
+                     const double* w11, int w11_stride, double w12, double* gl_lvl, cudaStream_t s);
+void launch_grad_pair(const DevGeom& G, const GlobalLayout& gl, int L, int B, double w, const double* a,
+                      const double* b, double* gl_lvl, cudaStream_t s);
+void launch_strip_adj_post(const DevGeom& G, const GlobalLayout& gl, int L, int B, double* utbar, const double* sbar,
+                           cudaStream_t s);
+void launch_grad_local(const DevGeom& G, const GlobalLayout& gl, int L, int B, const double* T_, const double* E,
+                       int use64, const double* uin, double* gl_lvl, cudaStream_t s);
+void launch_rbar(const DevGeom& G, const GlobalLayout& gl, int L, int B, const double* T_, int use64, double* rbar,
+                 cudaStream_t s);
+int adj_uin_blocks(const GlobalLayout& gl, int L);
+void launch_adj_uin(const DevGeom& G, const GlobalLayout& gl, int L, int B, double* utbar, const double* sbar,
+                    const double* rbar, const double* uin, const double* lam, int lam_stride, double* lbpart,
+                    int nblk_stride, cudaStream_t s);
+void launch_lambar_finalize(int B, int nblk, int nblk_stride, const double* lbpart, double* lambar, int lam_stride,
+                            int k, cudaStream_t s);
+void launch_lambar_init(int B, int n, const double* dl, double* lambar, cudaStream_t s);
+void launch_restrict_adj(const DevGeom& G, const GlobalLayout& gl, int k, int B, const double* fine, double* coarse,
+                         cudaStream_t s);
+template <typename T>
+void launch_level1_adj(const DevGeom& G, const GlobalLayout& gl, const Level1AdjArgs& a, cudaStream_t s);
+void launch_grad_spread(const DevGeom& G, const GlobalLayout& gl, int n, int B, const GradLevels& lv,
+                        const double* glbase, int layout, double* out, cudaStream_t s);
+
 }  // namespace mlev

@@ -86,6 +86,7 @@ struct GlobalLayout {
 #define MLEV_ST_RR_BREAKDOWN 4
 #define MLEV_ST_NONFINITE 8
 #define MLEV_ST_TIMEOUT 16  // a bounded wait on a TMA transaction barrier gave up
+#define MLEV_ST_ADJ_NOCONV 32  // the level-1 adjoint solve reached its iteration cap
 
 // Per-problem status record (long long slots), stride mlev_stat_stride(n).
 #define MLEV_STAT_L1_IT 0     // level-1 iterations

@@ -521,6 +521,30 @@ std::string Plan::build(const mlev_opts& o) {
   take(w_out_u, (size_t)B * (lvl_nx(n) + 1) * (lvl_ny(n) + 1) * 8);
   take(w_cinv, sub_direct ? (size_t)B * m * nd_max * nd_max * tsize : 0);
   ws_bytes = cur;
+  // ---- adjoint regions (only mlev_grad_kappa touches them) ----
+  const size_t ncoef = (size_t)(ncx + 1) * (ncy + 1);
+  take(g_ck_ut, (size_t)n * gbytes);                // u~_k of levels 1..n
+  take(g_ck_c, (size_t)(n + 1) * B * ncoef * 8);    // coarse coefficients of u_{h_k}, k = 0..n
+  take(g_ck_c0, (size_t)(n + 1) * B * 8);
+  take(g_ubar[0], gbytes);
+  take(g_ubar[1], gbytes);
+  take(g_utbar, gbytes);
+  take(g_sbar, gbytes);
+  take(g_rbar, gbytes);
+  take(g_tbuf, tsize == 4 ? (size_t)p64max * 8 : (size_t)pmax * 8);
+  long long glacc = 0;
+  for (int l = 1; l <= n; ++l) {
+    gl_off[l] = glacc;
+    glacc += (long long)B * lvl_nx(l) * lvl_ny(l) * 2;
+  }
+  take(g_gl, (size_t)glacc * 8);
+  take(g_coef, (size_t)B * (3 * ncoef + 8) * 8);
+  take(g_part2, (size_t)B * ncx * ncy * 5 * 8);
+  adj_nblk = ((lvl_nx(n) + 1 + 31) / 32) * ((lvl_ny(n) + 1 + 7) / 8);
+  take(g_lbpart, (size_t)B * adj_nblk * 8);
+  take(g_lambar, (size_t)B * (n + 1) * 8);
+  take(g_rrscr, (size_t)B * ((size_t)nhb * (bw + 1) + 10 * (size_t)nhb) * 8);
+  ws_grad_bytes = cur;
   return "";
 }
 

@@ -94,6 +94,12 @@ struct Plan {
   Span w_x, w_f, w_x64, w_aug, w_lam, w_c, w_c0, w_stat, w_jobnorm, w_chol, w_out_lam, w_out_u, w_cinv, w_tmaps;
   size_t ws_bytes = 0;
   size_t tables_bytes = 0;
+  // adjoint (mlev_grad_kappa): extra regions after the solve's, up to ws_grad_bytes
+  Span g_ck_ut, g_ck_c, g_ck_c0, g_ubar[2], g_utbar, g_sbar, g_rbar, g_tbuf, g_gl, g_coef, g_part2, g_lbpart,
+      g_lambar, g_rrscr;
+  long long gl_off[MLEV_MAX_LEVELS + 1] = {0};  // element offset of level l's triangle gradients in g_gl
+  int adj_nblk = 0;                              // partial-sum slots per problem (largest level grid)
+  size_t ws_grad_bytes = 0;
   KappaDev kap_template{};  // offsets relative to the workspace base
 
   std::string build(const mlev_opts& o);   // "" on success, else a message

@@ -25,8 +25,10 @@ MAX_LEVELS = 10
 
 EXPORTS = ["mlev_opts_default", "mlev_create", "mlev_destroy", "mlev_last_error", "mlev_set_domain",
            "mlev_set_partition", "mlev_set_levels", "mlev_set_forms", "mlev_workspace_size", "mlev_problem_info",
-           "mlev_solve", "mlev_solve_host", "mlev_profile_read", "mlev_solve_noalloc"]
+           "mlev_solve", "mlev_solve_host", "mlev_profile_read", "mlev_solve_noalloc", "mlev_grad_workspace_size",
+           "mlev_grad_kappa"]
 NOALLOC_WORKSPACE_BYTES = 32 << 20
+GRAD_FINE_ELEM, GRAD_COARSE_CELL = 0, 1
 
 
 class Opts(C.Structure):
@@ -97,9 +99,11 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.mlev_solve_host.argtypes = [P, C.POINTER(Opts), VP, SZ, VP, VP, VP, VP, C.POINTER(Report)]
     lib.mlev_profile_read.argtypes = [P, C.POINTER(KernelStat), I, C.POINTER(I)]
     lib.mlev_solve_noalloc.argtypes = [P, C.POINTER(Opts), VP, VP, VP, C.POINTER(Report)]
+    lib.mlev_grad_workspace_size.argtypes = [P, C.POINTER(Opts), C.POINTER(SZ)]
+    lib.mlev_grad_kappa.argtypes = [P, C.POINTER(Opts), VP, SZ, VP, VP, I, VP, VP, C.POINTER(Report)]
     for name in ("mlev_create", "mlev_set_domain", "mlev_set_partition", "mlev_set_levels", "mlev_set_forms",
                  "mlev_workspace_size", "mlev_problem_info", "mlev_solve", "mlev_solve_host", "mlev_profile_read",
-                 "mlev_solve_noalloc"):
+                 "mlev_solve_noalloc", "mlev_grad_workspace_size", "mlev_grad_kappa"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -188,10 +192,15 @@ class Solver:
         self._check(self.lib.mlev_workspace_size(self.h, C.byref(opts), C.byref(b)))
         return b.value
 
-    def workspace(self, opts: Opts):
+    def grad_workspace_bytes(self, opts: Opts) -> int:
+        b = C.c_size_t()
+        self._check(self.lib.mlev_grad_workspace_size(self.h, C.byref(opts), C.byref(b)))
+        return b.value
+
+    def workspace(self, opts: Opts, grad: bool = False):
         import torch
 
-        need = self.workspace_bytes(opts)
+        need = self.grad_workspace_bytes(opts) if grad else self.workspace_bytes(opts)
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
             assert self._ws.data_ptr() % 256 == 0
@@ -256,6 +265,106 @@ class Solver:
                                       C.byref(rep) if rep is not None else None)
         self._check(rc)
         return rep.as_dict() if rep is not None else None
+
+
+    def grad_shape(self, layout: int):
+        p = self.problem
+        if layout == GRAD_COARSE_CELL:
+            return (p.batch, p.ncy, p.ncx)
+        return (p.batch, p.ncy << p.levels, p.ncx << p.levels, 2)
+
+    def grad_kappa(self, opts: Opts | None = None, dlambda=None, layout: int | None = None, stream=None,
+                   report: bool = False):
+        """mlev_grad_kappa: (dkappa, lambda, report) with dkappa = dlambda_b * dlambda_{h_n}/dkappa on the
+        device. ``layout`` defaults to per coarse cell for a per-cell kappa, else per finest triangle."""
+        import torch
+
+        opts = opts or default_opts()
+        p = self.problem
+        if layout is None:
+            layout = GRAD_COARSE_CELL if p.kappa_kind == KAPPA_PER_COARSE_CELL else GRAD_FINE_ELEM
+        dev = f"cuda:{self.device}"
+        if dlambda is None:
+            dlambda = torch.ones(p.batch, dtype=torch.float64, device=dev)
+        assert dlambda.is_cuda and dlambda.dtype == torch.float64 and dlambda.is_contiguous()
+        assert dlambda.numel() == p.batch
+        ws = self.workspace(opts, grad=True)
+        dk = torch.empty(self.grad_shape(layout), dtype=torch.float64, device=dev)
+        lam = torch.empty(p.batch, dtype=torch.float64, device=dev)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        rep = Report() if report else None
+        rc = self.lib.mlev_grad_kappa(self.h, C.byref(opts), C.c_void_p(ws.data_ptr()), ws.numel(),
+                                      C.c_void_p(s.cuda_stream), C.c_void_p(dlambda.data_ptr()), layout,
+                                      C.c_void_p(dk.data_ptr()), C.c_void_p(lam.data_ptr()),
+                                      C.byref(rep) if rep is not None else None)
+        self._check(rc)
+        return dk, lam, (rep.as_dict() if rep is not None else None)
+
+    def set_kappa(self, kappa):
+        """Copy new coefficient values into the device buffer this solver was created with
+        (``kappa_device``); the next solve reads them."""
+        if self.kappa_device is None:
+            raise MlevError(-7, "set_kappa needs a solver created with kappa_device")
+        self.kappa_device.copy_(kappa.reshape(self.kappa_device.shape))
+
+
+def kappa_solver(problem, device: int = 0) -> Solver:
+    """A Solver whose coefficient lives in a device buffer (initialised from problem.kappa),
+    as ``LambdaFn`` needs."""
+    import torch
+
+    if problem.kappa_kind == KAPPA_ONE:
+        raise MlevError(-1, "the problem has no coefficient array (kappa_kind ONE)")
+    buf = torch.tensor(np.ascontiguousarray(problem.kappa, dtype=np.float64), device=f"cuda:{device}")
+    return Solver(problem, device=device, kappa_device=buf)
+
+
+def _autograd_function():
+    import torch
+
+    class LambdaFn(torch.autograd.Function):
+        """lambda_{h_n}[b] of Algorithm 4.2 as a differentiable function of the coefficient.
+
+        ``LambdaFn.apply(kappa, solver, opts)``: kappa has the shape of the solver's problem
+        kappa ([B][ncy][ncx] per coarse cell or [B][fny][fnx][2] per finest triangle) and
+        lives on the solver's device; ``solver`` comes from ``kappa_solver``. The backward
+        pass is mlev_grad_kappa with the incoming gradient as upstream weights.
+        """
+
+        @staticmethod
+        def forward(ctx, kappa, solver, opts):
+            solver.set_kappa(kappa.detach())
+            lam, _ = solver.alloc_outputs()
+            solver.solve_into(opts, lam)
+            ctx.solver, ctx.opts = solver, opts
+            ctx.save_for_backward(kappa.detach().clone())
+            return lam
+
+        @staticmethod
+        def backward(ctx, g):
+            (kappa,) = ctx.saved_tensors
+            ctx.solver.set_kappa(kappa)
+            dk, _, _ = ctx.solver.grad_kappa(ctx.opts, g.detach().to(torch.float64).contiguous())
+            return dk.reshape(kappa.shape), None, None
+
+    return LambdaFn
+
+
+def __getattr__(name):
+    if name == "LambdaFn":
+        fn = _autograd_function()
+        globals()["LambdaFn"] = fn
+        return fn
+    raise AttributeError(name)
+
+
+def eigensolve(problem, opts: Opts | None = None, want_u: bool = False, device: int = 0):
+    """One-call solve: (lambda [B], u [B, ny+1, nx+1] or None, report)."""
+    s = Solver(problem, device=device)
+    try:
+        return s.solve(opts, want_u=want_u)
+    finally:
+        s.close()
 
 
 def profile_read(solver: "Solver") -> list[dict]:
