@@ -48,7 +48,9 @@ def fp64_opts(mlev, graph=1):
 
 # ------------------------------------------------------------------ helpers
 def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    from paper_1401_4969_gb300 import replicas
+
+    return replicas.env_ranks()
 
 
 def measured_peaks():
@@ -215,7 +217,7 @@ def main():
                                     stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
 
     import workloads as W
-    from paper_1401_4969_gb300 import mlev
+    from paper_1401_4969_gb300 import mlev, replicas
 
     p = W.config2()
     solver = mlev.Solver(p, device=local_rank)
@@ -247,11 +249,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return replicas.max_over_ranks(ms, dist, "cuda")
 
     om = mixed_opts(mlev)
     rep = solver.solve_into(mixed_opts(mlev, graph=0), lam, None, stream, report=True)
@@ -294,11 +292,7 @@ def main():
         t0 = time.perf_counter()
         solver.solve_host(oh, lam_h, u_h)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_ms = 1e3 * statistics.mean(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replicas.max_over_ranks(1e3 * statistics.mean(e2e_t), dist, "cuda")
     h2d, d2h = int(io["h2d_bytes"]), int(io["d2h_bytes"])
 
     # profiled pass: per-kernel-family CUDA-event times on the solve's stream
