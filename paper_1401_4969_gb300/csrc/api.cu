@@ -352,7 +352,18 @@ struct Launcher {
       a.c0 = c0L(1);
       a.stat = stat;
       a.stat_stride = stat_stride;
-      go(F_LEVEL1, 0.0, [&] { launch_level1<T>(G, P.glay, a, s); });
+      long long nn0 = 0, tot = 0;
+      for (int k = 0; k < P.l1_nlev; ++k) {
+        const GridDesc& gk = P.grids[P.l1_grid_begin + k];
+        const long long nk = (long long)(gk.nx + 1) * (gk.ny + 1);
+        if (k == 0) nn0 = nk;
+        tot += (nk + 1) & ~1LL;
+      }
+      const size_t l1smem = level1_smem_bytes(nn0, tot, sizeof(T));
+      if (l1smem <= (size_t)kL1SmemMax)
+        go(F_LEVEL1, 0.0, [&] { launch_level1_sm<T>(G, P.glay, a, l1smem, s); });
+      else
+        go(F_LEVEL1, 0.0, [&] { launch_level1<T>(G, P.glay, a, s); });
     }
     T* X = at<T>(ws, P.w_x);
     T* F = at<T>(ws, P.w_f);
@@ -429,7 +440,8 @@ struct Launcher {
       rr.stat = stat;
       rr.stat_stride = stat_stride;
       rr.max_iter = o.rr_max_iter;
-      rr.smem = rr_smem_bytes(P.nhb, P.bw) <= (size_t)kRRSmemMax;
+      rr.mixed = (mixed && rr_mixed_supported(P.nhb, P.bw)) ? 1 : 0;
+      rr.smem = (rr.mixed ? rr_mixed_smem_bytes(P.nhb, P.bw) : rr_smem_bytes(P.nhb, P.bw)) <= (size_t)kRRSmemMax;
       go(F_RR, 0.0, [&] { launch_rr(G, rr, s); });
     }
     go(F_OUT, 16.0 * B, [&] { launch_lambda_out(B, n, lam, lambda_out, s); });

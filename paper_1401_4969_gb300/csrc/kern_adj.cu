@@ -529,8 +529,8 @@ __global__ void __launch_bounds__(256) k_restrict_adj(DevGeom G, GlobalLayout gl
 // Pi = I - u (M u)^T (onto the M-orthogonal complement of u) and Pi^T = I - (M u) u^T.
 template <typename T, int KK>
 __global__ void __launch_bounds__(1024) k_level1_adj(DevGeom G, GlobalLayout gl, Level1AdjArgs a) {
-  __shared__ double scratch[32 * 3];
-  __shared__ double red[3];
+  __shared__ double scratch[32 * 4];
+  __shared__ double red[4];
   const int p = blockIdx.x;
   const int g0 = a.grid_begin + p * a.nlev;
   const GridDesc& g = G.grids[g0];
@@ -642,18 +642,24 @@ __global__ void __launch_bounds__(1024) k_level1_adj(DevGeom G, GlobalLayout gl,
       }
       if (!(pap > 0.0)) break;
       const double alpha = rho / pap;
+      // convergence on Pi^T r: u is an eigenvector only up to the level-1 eigen-residual, so
+      // the component of r along M u is the system's inconsistency, not solver error
       double rr;
       {
-        double v[1] = {0.0};
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
         for (int q = threadIdx.x; q < nn; q += blockDim.x) {
           const long long c = cidx(q);
           Z[c] += alpha * P[c];
           R[c] -= alpha * AP[c];
           WO[c] = W[c];
           v[0] += R[c] * R[c];
+          v[1] += U[c] * R[c];
+          v[2] += MU[c] * R[c];
+          v[3] += MU[c] * MU[c];
         }
-        block_sum<1>(v, scratch, red);
-        rr = red[0];
+        block_sum<4>(v, scratch, red);
+        const double cu = red[1] / umu;
+        rr = fmax(red[0] - 2.0 * cu * red[2] + cu * cu * red[3], 0.0);
       }
       if (rr <= a.tol * a.tol * rr0) {
         conv = true;

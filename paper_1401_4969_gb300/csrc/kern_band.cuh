@@ -74,4 +74,67 @@ __device__ __forceinline__ void band_fwd(const double* Lb, const double* invD, d
   __syncthreads();
 }
 
+// FP32 band LDL^T of S (no right-hand side), same storage and schedule as band_ldlt (one
+// block barrier per column; a thread keeps its (i - j, k - j) pair for every column, which
+// needs npair <= blockDim.x). The pivots' reciprocals are the fast approximate ones: the
+// factors only precondition FP64 iterative refinement. Returns false (to all threads) on a
+// non-positive pivot.
+__device__ inline bool band_ldlt_f(float* Lb, float* invD, const int* pairs, int npair, int N, int bw) {
+  const int bw1 = bw + 1;
+  const bool mine = threadIdx.x < npair;
+  const int aa = mine ? pairs[threadIdx.x] >> 16 : 0, bb = mine ? pairs[threadIdx.x] & 0xffff : 0;
+  __syncthreads();
+  for (int j = 0; j < N; ++j) {
+    const float Dj = Lb[j * bw1];
+    if (!(Dj > 0.f)) return false;  // identical decision in every thread
+    const float inv = __fdividef(1.0f, Dj);
+    const int i = j + 1 + aa, k = j + 1 + bb;
+    if (mine && i <= min(N - 1, j + bw))
+      Lb[i * bw1 + (i - k)] -= Lb[i * bw1 + (i - j)] * Lb[k * bw1 + (k - j)] * inv;
+    if (threadIdx.x == 0) invD[j] = inv;
+    __syncthreads();
+  }
+  return true;
+}
+
+// S x = b in place with FP32 factors whose off-diagonal band entries were pre-scaled to
+// L(i, i-d) = Ls[i * ls + d], by warp 0 with the active part of the right-hand side in
+// registers (needs bw <= 31). Entry e lives in lane e mod 32; at column j the head lane
+// j mod 32 holds the final z_j, every lane holding an entry j + d (1 <= d <= bw) subtracts
+// L(j + d, j) z_j, and the head lane then takes entry j + 32. One shuffle per step. Back
+// substitution runs the same way from the bottom with t = D^{-1} z.
+__device__ inline void band_solve_shfl(const float* Ls, int ls, const float* invD, float* y, int N, int bw) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    float v = lane < N ? y[lane] : 0.f;
+#pragma unroll 4
+    for (int j = 0; j < N; ++j) {
+      // loads independent of v first; the head lane's refill and the store of z_j are
+      // done without branching (every lane stores the same value)
+      const int h = j & 31, d = (lane - j) & 31;
+      const float coef = (d >= 1 && d <= bw && j + d < N) ? Ls[(j + d) * ls + d] : 0.f;
+      const float refill = (j + 32 < N) ? y[j + 32] : 0.f;
+      const float dj = invD[j];
+      const float zj = __shfl_sync(full, v, h);
+      v = (lane == h) ? refill : v - coef * zj;
+      y[j] = zj * dj;
+    }
+    __syncwarp();
+    // entry i lives in lane (N - 1 - i) mod 32; x_i final at the head, entries i - d take
+    // the update -L(i, i - d) x_i
+    v = (N - 1 - lane >= 0) ? y[N - 1 - lane] : 0.f;
+#pragma unroll 4
+    for (int i = N - 1; i >= 0; --i) {
+      const int h = (N - 1 - i) & 31, d = (lane - (N - 1 - i)) & 31;
+      const float coef = (d >= 1 && d <= bw && i - d >= 0) ? Ls[i * ls + d] : 0.f;
+      const float refill = (i - 32 >= 0) ? y[i - 32] : 0.f;
+      const float xi = __shfl_sync(full, v, h);
+      v = (lane == h) ? refill : v - coef * xi;
+      y[i] = xi;
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace mlev

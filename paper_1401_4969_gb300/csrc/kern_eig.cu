@@ -18,6 +18,7 @@
 //   c = [-S(mu)^{-1} w ; 1], scaled to b(u,u) = 1 and int u > 0.
 #include "kern_band.cuh"
 #include "kern_blk.cuh"
+#include "kern_tail.cuh"
 #include "kern_launch.h"
 
 namespace mlev {
@@ -102,6 +103,93 @@ __device__ bool small_geneig(int n, const double A[3][3], const double B[3][3], 
   }
   for (int i = 0; i < n; ++i) coef[i] = d[i] * y[i];
   for (int i = n; i < 3; ++i) coef[i] = 0.0;
+  return true;
+}
+
+// Same computation in either precision (R = float or double); off_tol is the relative size
+// of the off-diagonal part at which the Jacobi sweeps stop.
+// Smallest eigenpair of the symmetric-definite pencil (A, B) of order n <= 3 with
+// symmetric diagonal scaling, Cholesky of B and cyclic Jacobi rotations. Returns false
+// if B is numerically singular.
+template <typename R>
+__device__ bool small_geneig_t(int n, const R A[3][3], const R B[3][3], R& theta, R coef[3], R off_tol) {
+  R d[3], As[3][3], Bs[3][3], Lc[3][3] = {{0}}, C[3][3], V[3][3];
+  for (int i = 0; i < n; ++i) d[i] = (R)1 / sqrt(B[i][i]);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      As[i][j] = A[i][j] * d[i] * d[j];
+      Bs[i][j] = B[i][j] * d[i] * d[j];
+    }
+  for (int j = 0; j < n; ++j) {
+    R s = Bs[j][j];
+    for (int k = 0; k < j; ++k) s -= Lc[j][k] * Lc[j][k];
+    if (!(s > (R)1e-10)) return false;
+    Lc[j][j] = sqrt(s);
+    for (int i = j + 1; i < n; ++i) {
+      R t = Bs[i][j];
+      for (int k = 0; k < j; ++k) t -= Lc[i][k] * Lc[j][k];
+      Lc[i][j] = t / Lc[j][j];
+    }
+  }
+  // C = L^{-1} As L^{-T}: Y = L^{-1} As, then C = (L^{-1} Y^T)^T
+  R Y[3][3];
+  for (int c = 0; c < n; ++c)
+    for (int i = 0; i < n; ++i) {
+      R t = As[i][c];
+      for (int k = 0; k < i; ++k) t -= Lc[i][k] * Y[k][c];
+      Y[i][c] = t / Lc[i][i];
+    }
+  for (int r = 0; r < n; ++r)
+    for (int i = 0; i < n; ++i) {
+      R t = Y[r][i];
+      for (int k = 0; k < i; ++k) t -= Lc[i][k] * C[r][k];
+      C[r][i] = t / Lc[i][i];
+    }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[i][j] = (R)(i == j);
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    R off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += C[p][q] * C[p][q];
+    R dg = (R)0;
+    for (int p = 0; p < n; ++p) dg += C[p][p] * C[p][p];
+    if (off <= off_tol * dg) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (C[p][q] == 0.0) continue;
+        const R tau = (C[q][q] - C[p][p]) / ((R)2 * C[p][q]);
+        const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+        const R cs = (R)1 / sqrt((R)1 + t * t), sn = t * cs;
+        for (int k = 0; k < n; ++k) {
+          const R a = C[k][p], b = C[k][q];
+          C[k][p] = cs * a - sn * b;
+          C[k][q] = sn * a + cs * b;
+        }
+        for (int k = 0; k < n; ++k) {
+          const R a = C[p][k], b = C[q][k];
+          C[p][k] = cs * a - sn * b;
+          C[q][k] = sn * a + cs * b;
+        }
+        for (int k = 0; k < n; ++k) {
+          const R a = V[k][p], b = V[k][q];
+          V[k][p] = cs * a - sn * b;
+          V[k][q] = sn * a + cs * b;
+        }
+      }
+  }
+  int im = 0;
+  for (int i = 1; i < n; ++i)
+    if (C[i][i] < C[im][im]) im = i;
+  theta = C[im][im];
+  // coef = D L^{-T} v
+  R y[3];
+  for (int i = n - 1; i >= 0; --i) {
+    R t = V[i][im];
+    for (int k = i + 1; k < n; ++k) t -= Lc[k][i] * y[k];
+    y[i] = t / Lc[i][i];
+  }
+  for (int i = 0; i < n; ++i) coef[i] = d[i] * y[i];
+  for (int i = n; i < 3; ++i) coef[i] = (R)0;
   return true;
 }
 
@@ -286,6 +374,275 @@ void launch_level1(const DevGeom& G, const GlobalLayout& gl, const Level1Args& a
 template void launch_level1<float>(const DevGeom&, const GlobalLayout&, const Level1Args&, cudaStream_t);
 template void launch_level1<double>(const DevGeom&, const GlobalLayout&, const Level1Args&, cudaStream_t);
 
+// ---------------------------------------------------------------- level-1 LOBPCG on chip
+// The same iteration as k_level1 with every vector and the whole level-1 multigrid
+// hierarchy in shared memory (compact row pitch nx + 1); used when they fit.
+// Layout: 10 FP64 vectors of the level-1 grid, then x (T) of every level, f (T) of every
+// level, then the unknown masks.
+template <typename T, int KK>
+__global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, Level1Args a) {
+  extern __shared__ __align__(16) unsigned char l1_raw[];
+  __shared__ SmGrid<T> lv[kTailMaxLev];
+  __shared__ double scratch[16 * 12];
+  __shared__ double red[12];
+  __shared__ double sh_coef[4];
+  __shared__ int sh_flag;
+  const int p = blockIdx.x, g0 = a.grid_begin + p * a.nlev, nlev = a.nlev;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const GridDesc& g = G.grids[g0];
+  const int nx = g.nx, ny = g.ny, W = nx + 1, nn = W * (ny + 1);
+  double* G12 = reinterpret_cast<double*>(l1_raw);  // [12][threads] Gram partial sums
+  double* X = G12 + 12 * nt;
+  double *Wv = X + nn, *P = Wv + nn, *KX = P + nn, *MX = KX + nn, *KW = MX + nn, *MW = KW + nn, *KP = MW + nn,
+         *MP = KP + nn, *R = MP + nn;
+  if (tid == 0) {
+    long long tot = 0;
+    for (int k = 0; k < nlev; ++k) {
+      const GridDesc& gk = G.grids[g0 + k];
+      tot += ((long long)(gk.nx + 1) * (gk.ny + 1) + 1) & ~1LL;
+    }
+    T* xb = reinterpret_cast<T*>(R + nn);
+    T* fb = xb + tot;
+    uint8_t* mb = reinterpret_cast<uint8_t*>(fb + tot);
+    long long off = 0;
+    for (int k = 0; k < nlev; ++k) {
+      const GridDesc& gk = G.grids[g0 + k];
+      lv[k].x = xb + off;
+      lv[k].f = fb + off;
+      lv[k].m = mb + off;
+      lv[k].nx = gk.nx;
+      lv[k].ny = gk.ny;
+      lv[k].W = gk.nx + 1;
+      lv[k].g = &G.grids[g0 + k];
+      off += ((long long)(gk.nx + 1) * (gk.ny + 1) + 1) & ~1LL;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < nlev; ++k) {
+    const GridDesc& gk = *lv[k].g;
+    const int nk = lv[k].W * (lv[k].ny + 1);
+    for (int q = tid; q < nk; q += nt) {
+      const int j = q / lv[k].W, i = q - j * lv[k].W;
+      lv[k].m[q] = is_unknown(G, gk, i, j);
+    }
+  }
+  __syncthreads();
+  const uint8_t* m0 = lv[0].m;
+  const double h = level_h(G.H, 1), m12 = h * h / 12.0;
+#define L1_FOR_NODES for (int j = threadIdx.y; j <= ny; j += blockDim.y) for (int i = threadIdx.x; i <= nx; i += blockDim.x)
+  auto apply_km = [&](const double* v, double* kv, double* mv) {
+    L1_FOR_NODES {
+      const int q = j * W + i;
+      if (!m0[q]) {
+        kv[q] = 0.0;
+        mv[q] = 0.0;
+        continue;
+      }
+      const W4 w = edge_weights<KK>(G.kap, p, 1, g.ox + i, g.oy + j);
+      kv[q] = (w.e + w.w + w.n + w.s) * v[q] - w.e * v[q + 1] - w.w * v[q - 1] - w.n * v[q + W] - w.s * v[q - W];
+      mv[q] = m12 * (6.0 * v[q] + v[q + 1] + v[q - 1] + v[q + W] + v[q - W] + v[q + W + 1] + v[q - W - 1]);
+    }
+    __syncthreads();
+  };
+  L1_FOR_NODES {
+    const int q = j * W + i;
+    X[q] = m0[q] ? 1.0 : 0.0;
+    Wv[q] = P[q] = KP[q] = MP[q] = R[q] = 0.0;
+  }
+  __syncthreads();
+  apply_km(X, KX, MX);
+  double rho;
+  {
+    double v[2] = {0.0, 0.0};
+    L1_FOR_NODES {
+      const int q = j * W + i;
+      v[0] += X[q] * KX[q];
+      v[1] += X[q] * MX[q];
+    }
+    block_sum_2d<2>(v, scratch, red);
+    rho = red[0] / red[1];
+  }
+  bool have_p = false;
+  int it = 0;
+  double res = 1.0;
+  for (; it < a.max_iter; ++it) {
+    if (it > 0) {  // FP64 Rayleigh quotient of the current x
+      double v[2] = {0.0, 0.0};
+      L1_FOR_NODES {
+        const int q = j * W + i;
+        v[0] += X[q] * KX[q];
+        v[1] += X[q] * MX[q];
+      }
+      block_sum_2d<2>(v, scratch, red);
+      rho = red[0] / red[1];
+    }
+    {
+      double v[2] = {0.0, 0.0};
+      L1_FOR_NODES {
+        const int q = j * W + i;
+        const double r = KX[q] - rho * MX[q];
+        R[q] = r;
+        v[0] += r * r;
+        v[1] += MX[q] * MX[q];
+      }
+      block_sum_2d<2>(v, scratch, red);
+      res = sqrt(red[0]) / (rho * sqrt(red[1]));
+    }
+    if (res < a.tol) break;
+    // preconditioner: one V-cycle for K w = r from w = 0, all grids on chip
+    L1_FOR_NODES {
+      const int q = j * W + i;
+      lv[0].f[q] = m0[q] ? (T)R[q] : (T)0;
+      lv[0].x[q] = (T)0;
+    }
+    __syncthreads();
+    for (int d = 0; d + 1 < nlev; ++d) {
+      tail_smooth<T, KK>(G, lv[d], a.pre, false, (T)a.omega);
+      tail_restrict<T, KK>(G, lv[d], lv[d + 1]);
+    }
+    tail_smooth<T, KK>(G, lv[nlev - 1], a.coarse_sweeps, false, (T)a.omega);
+    for (int d = nlev - 2; d >= 0; --d) {
+      tail_prolong<T>(lv[d], lv[d + 1]);
+      tail_smooth<T, KK>(G, lv[d], a.post, true, (T)a.omega);
+    }
+    L1_FOR_NODES {
+      const int q = j * W + i;
+      Wv[q] = (double)lv[0].x[q];
+    }
+    __syncthreads();
+    apply_km(Wv, KW, MW);
+    {
+      double v[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = 0.0;
+      L1_FOR_NODES {
+        const int q = j * W + i;
+        const double x = X[q], w = Wv[q], pp = P[q];
+        v[0] += x * KX[q]; v[1] += x * KW[q]; v[2] += x * KP[q];
+        v[3] += w * KW[q]; v[4] += w * KP[q]; v[5] += pp * KP[q];
+        v[6] += x * MX[q]; v[7] += x * MW[q]; v[8] += x * MP[q];
+        v[9] += w * MW[q]; v[10] += w * MP[q]; v[11] += pp * MP[q];
+      }
+      // transposed reduction: warp k sums entry k over all threads
+#pragma unroll
+      for (int k = 0; k < 12; ++k) G12[k * nt + tid] = v[k];
+      __syncthreads();
+      const int lane = tid & 31, warp = tid >> 5;
+      if (warp < 12) {
+        double s = 0.0;
+        for (int q = lane; q < nt; q += 32) s += G12[warp * nt + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp] = s;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      // Ritz pair of the 3 x 3 pencil (A - rho B, B) in FP32: the shift by the FP64 Rayleigh
+      // quotient removes the common part, so FP32 resolves the small coefficients of w and
+      // p (a coefficient error only makes the step slightly suboptimal; rho itself is
+      // recomputed in FP64 from the vectors)
+      const double A[3][3] = {{red[0], red[1], red[2]}, {red[1], red[3], red[4]}, {red[2], red[4], red[5]}};
+      const double Bm[3][3] = {{red[6], red[7], red[8]}, {red[7], red[9], red[10]}, {red[8], red[10], red[11]}};
+      float As[3][3], Bs[3][3], ths, cfs[3];
+      for (int r2 = 0; r2 < 3; ++r2)
+        for (int c2 = 0; c2 < 3; ++c2) {
+          As[r2][c2] = (float)(A[r2][c2] - rho * Bm[r2][c2]);
+          Bs[r2][c2] = (float)Bm[r2][c2];
+        }
+      bool ok = have_p && small_geneig_t<float>(3, As, Bs, ths, cfs, 1e-12f);
+      if (!ok) ok = small_geneig_t<float>(2, As, Bs, ths, cfs, 1e-12f);
+      double th = rho + (double)ths, cf[3] = {cfs[0], cfs[1], cfs[2]};
+      // near-dependent x, w, p defeat the FP32 Gram factorization: FP64 as before
+      if (!ok && have_p) ok = small_geneig(3, A, Bm, th, cf);
+      if (!ok) ok = small_geneig(2, A, Bm, th, cf);
+      if (!ok) {
+        th = rho;
+        cf[0] = 1.0;
+        cf[1] = cf[2] = 0.0;
+      }
+      const float bx = (float)(cf[0] * cf[0] * Bm[0][0] + cf[1] * cf[1] * Bm[1][1] + cf[2] * cf[2] * Bm[2][2] +
+                               2.0 * (cf[0] * cf[1] * Bm[0][1] + cf[0] * cf[2] * Bm[0][2] + cf[1] * cf[2] * Bm[1][2]));
+      const float bp = (float)(cf[1] * cf[1] * Bm[1][1] + cf[2] * cf[2] * Bm[2][2] + 2.0 * cf[1] * cf[2] * Bm[1][2]);
+      const double sx = (double)rsqrtf(bx), sp = bp > 0.f ? (double)rsqrtf(bp) : 0.0;
+      sh_coef[0] = cf[0] * sx;
+      sh_coef[1] = cf[1];
+      sh_coef[2] = cf[2];
+      sh_coef[3] = th;
+      red[0] = sx;
+      red[1] = sp;
+      sh_flag = ok && bp > 0;
+    }
+    __syncthreads();
+    const double ca = sh_coef[0], cb = sh_coef[1], cp = sh_coef[2], sx = red[0], sp = red[1];
+    L1_FOR_NODES {
+      const int q = j * W + i;
+      const double pn = cb * Wv[q] + cp * P[q], kpn = cb * KW[q] + cp * KP[q], mpn = cb * MW[q] + cp * MP[q];
+      X[q] = ca * X[q] + sx * pn;
+      KX[q] = ca * KX[q] + sx * kpn;
+      MX[q] = ca * MX[q] + sx * mpn;
+      P[q] = sp * pn;
+      KP[q] = sp * kpn;
+      MP[q] = sp * mpn;
+    }
+    rho = sh_coef[3];
+    have_p = sh_flag != 0;
+    __syncthreads();
+  }
+  apply_km(X, KX, MX);
+  double v[3] = {0.0, 0.0, 0.0};
+  L1_FOR_NODES {
+    const int q = j * W + i;
+    v[0] += X[q] * KX[q];
+    v[1] += X[q] * MX[q];
+    v[2] += X[q];
+  }
+  block_sum_2d<3>(v, scratch, red);
+  const double lam = red[0] / red[1];
+  const double sc = (red[2] >= 0 ? 1.0 : -1.0) / sqrt(red[1]);
+  double* out = a.ut1 + (long long)p * gl.bstride;
+  const int gp = gl.pitch[1 - MLEV_LMIN];
+  L1_FOR_NODES { out[(long long)j * gp + i] = sc * X[j * W + i]; }
+#undef L1_FOR_NODES
+  const int ncoef = (G.ncx + 1) * (G.ncy + 1);
+  for (int q = tid; q < ncoef; q += nt) a.c[(long long)p * ncoef + q] = 0.0;
+  if (tid == 0) {
+    a.c0[p] = 1.0;
+    a.lam[p * a.lam_stride + 1] = lam;
+    a.stat[p * a.stat_stride + MLEV_STAT_L1_IT] = it;
+    a.stat[p * a.stat_stride + MLEV_STAT_L1_RES] = (long long)__double_as_longlong(res);
+    if (it >= a.max_iter)
+      atomicOr((unsigned long long*)&a.stat[p * a.stat_stride + MLEV_STAT_FLAGS], (unsigned long long)MLEV_ST_LEVEL1_NOCONV);
+    if (!isfinite(lam))
+      atomicOr((unsigned long long*)&a.stat[p * a.stat_stride + MLEV_STAT_FLAGS], (unsigned long long)MLEV_ST_NONFINITE);
+  }
+}
+
+size_t level1_smem_bytes(long long nn0, long long tot, int tsize) {
+  return (size_t)(12 * 512 * 8 + 10 * nn0 * 8 + 2 * tot * tsize + tot + 16);
+}
+
+template <typename T>
+void launch_level1_sm(const DevGeom& G, const GlobalLayout& gl, const Level1Args& a, size_t smem, cudaStream_t s) {
+  switch (G.kap.kind) {
+#define L1_CASE(KKV)                                                                                     \
+  {                                                                                                      \
+    static bool attr = false;                                                                            \
+    if (!attr) {                                                                                         \
+      cudaFuncSetAttribute(k_level1_sm<T, KKV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kL1SmemMax); \
+      attr = true;                                                                                       \
+    }                                                                                                    \
+    k_level1_sm<T, KKV><<<a.B, dim3(32, 16), smem, s>>>(G, gl, a);                                       \
+  }
+    case MLEV_KAPPA_ONE: L1_CASE(MLEV_KAPPA_ONE) break;
+    case MLEV_KAPPA_PER_COARSE_CELL: L1_CASE(MLEV_KAPPA_PER_COARSE_CELL) break;
+    default: L1_CASE(MLEV_KAPPA_PER_FINE_ELEM) break;
+#undef L1_CASE
+  }
+}
+template void launch_level1_sm<float>(const DevGeom&, const GlobalLayout&, const Level1Args&, size_t, cudaStream_t);
+template void launch_level1_sm<double>(const DevGeom&, const GlobalLayout&, const Level1Args&, size_t, cudaStream_t);
+
 // ---------------------------------------------------------------- Rayleigh-Ritz
 __global__ void __launch_bounds__(256) k_rr(DevGeom G, RRArgs a) {
   extern __shared__ double rr_sm[];
@@ -436,6 +793,264 @@ __global__ void __launch_bounds__(256) k_rr(DevGeom G, RRArgs a) {
   }
 }
 
+// Mixed-precision Rayleigh-Ritz (MLEV_PREC_MIXED): the Newton iteration of k_rr with the
+// serial linear algebra moved off the FP64 pipe. S(sigma) is factored in FP32 (band
+// LDL^T); every solve S(mu) y = w(mu) is FP64 iterative refinement y += S(sigma)^{-1} r
+// (FP32 register-window solves by one warp), r = w - S(mu) y (FP64 band products from
+// K_H and M_H staged in shared memory). It converges while |mu - sigma| is small against
+// the distance of mu to the spectrum of (K_H, M_H); the factors are rebuilt at the current
+// mu when it stalls.
+// f(mu) is evaluated as alpha - mu beta - (w^T y + y^T r), the variational form of
+// w^T S^{-1} w, whose error is quadratic in the error of y.
+__global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
+  extern __shared__ double rr_sm[];
+  __shared__ double scratch[8 * 4];
+  __shared__ double red[4];
+  const int p = blockIdx.x, N = a.nhb, bw = a.bw, bw1 = bw + 1;
+  const int ncx = G.ncx, ncy = G.ncy;
+  const int npair = bw * (bw + 1) / 2;
+  double* base = a.smem ? rr_sm : a.chol + (long long)p * ((long long)N * bw1 + 5LL * N);
+  double* ga = base;
+  double* gb = ga + N;
+  double* wv = gb + N;
+  double* y = wv + N;
+  double* r = y + N;
+  double* kh_s = r + N;                                   // staged K_H, M_H (shared-memory mode)
+  double* mh_s = kh_s + (long long)N * bw1;
+  double* sm_s = mh_s + (long long)N * bw1;               // S(mu) of the current mu (FP64)
+  float* Lb = reinterpret_cast<float*>(a.smem ? sm_s + (long long)N * bw1 : r + N);
+  float* invD = Lb + (long long)N * bw1;
+  float* r32 = invD + N;
+  int* pairs = reinterpret_cast<int*>(a.smem ? reinterpret_cast<double*>(r32 + N + (N & 1)) : rr_sm);
+  const double* KH = a.KH + (long long)p * N * bw1;
+  const double* MH = a.MH + (long long)p * N * bw1;
+  if (a.smem) {
+    for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) {
+      kh_s[q] = KH[q];
+      mh_s[q] = MH[q];
+    }
+    KH = kh_s;
+    MH = mh_s;
+  }
+  double smu = NAN;  // mu of the S band in sm_s (shared-memory mode)
+  // r_q = w_q - (S(mu) y)_q, from the staged S(mu) band when it is current
+  auto resid_row = [&](const double* v, int q, double mu) {
+    if (a.smem && smu == mu) {
+      double s = sm_s[(long long)q * bw1] * v[q];
+      for (int d = 1; d <= bw; ++d) {
+        if (q - d >= 0) s += sm_s[(long long)q * bw1 + d] * v[q - d];
+        if (q + d < N) s += sm_s[(long long)(q + d) * bw1 + d] * v[q + d];
+      }
+      return wv[q] - s;
+    }
+    double sk = KH[(long long)q * bw1] * v[q], sm = MH[(long long)q * bw1] * v[q];
+    for (int d = 1; d <= bw; ++d) {
+      if (q - d >= 0) {
+        sk += KH[(long long)q * bw1 + d] * v[q - d];
+        sm += MH[(long long)q * bw1 + d] * v[q - d];
+      }
+      if (q + d < N) {
+        sk += KH[(long long)(q + d) * bw1 + d] * v[q + d];
+        sm += MH[(long long)(q + d) * bw1 + d] * v[q + d];
+      }
+    }
+    return wv[q] - (sk - mu * sm);
+  };
+  const double* part = a.partials + (long long)p * ncx * ncy * 12;
+  for (int q = threadIdx.x; q < npair; q += blockDim.x) {
+    int aa = 0;
+    while ((aa + 1) * (aa + 2) / 2 <= q) ++aa;
+    pairs[q] = (aa << 16) | (q - aa * (aa + 1) / 2);
+  }
+  {
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int q = threadIdx.x; q < ncx * ncy; q += blockDim.x) {
+      v[0] += part[q * 12 + 0];
+      v[1] += part[q * 12 + 1];
+      v[2] += part[q * 12 + 2];
+    }
+    block_sum<3>(v, scratch, red);
+  }
+  const double alpha = red[0], beta = red[1], sigma = red[2];
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    const int X = q % (ncx - 1) + 1, Y = q / (ncx - 1) + 1;
+    double sa = 0.0, sb = 0.0;
+    if (is_free(G, 0, ncx, ncy, X, Y)) {
+      const double* c11 = part + ((Y - 1) * ncx + (X - 1)) * 12;
+      const double* c01 = part + ((Y - 1) * ncx + X) * 12;
+      const double* c10 = part + (Y * ncx + (X - 1)) * 12;
+      const double* c00 = part + (Y * ncx + X) * 12;
+      sa = c00[3] + c10[4] + c01[5] + c11[6];
+      sb = c00[7] + c10[8] + c01[9] + c11[10];
+    }
+    ga[q] = sa;
+    gb[q] = sb;
+  }
+  __syncthreads();
+  auto band_mv = [&](const double* M, const double* v, int q) {
+    double s = M[(long long)q * bw1] * v[q];
+    for (int d = 1; d <= bw; ++d) {
+      if (q - d >= 0) s += M[(long long)q * bw1 + d] * v[q - d];
+      if (q + d < N) s += M[(long long)(q + d) * bw1 + d] * v[q + d];
+    }
+    return s;
+  };
+  double sig = NAN;  // shift of the current factors
+  // FP32 factors of S(mu), off-diagonals scaled to L; false if S(mu) is not positive definite
+  auto factor = [&](double mu) {
+    sig = mu;
+    for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) Lb[q] = (float)(KH[q] - mu * MH[q]);
+    if (!band_ldlt_f(Lb, invD, pairs, npair, N, bw)) return false;
+    for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) {
+      const int i = (int)(q / bw1), d = (int)(q % bw1);
+      if (d > 0 && i - d >= 0) Lb[q] *= invD[i - d];
+    }
+    __syncthreads();
+    return true;
+  };
+  // w = w(mu) and r = w - S(mu) y for the current y (the previous solution warm-starts the
+  // next solve; y starts at 0)
+  for (int q = threadIdx.x; q < N; q += blockDim.x) y[q] = 0.0;
+  __syncthreads();
+  auto start = [&](double mu) {
+    for (int q = threadIdx.x; q < N; q += blockDim.x) wv[q] = ga[q] - mu * gb[q];
+    if (a.smem && smu != mu) {
+      for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) sm_s[q] = kh_s[q] - mu * mh_s[q];
+      smu = mu;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < N; q += blockDim.x) r[q] = resid_row(y, q, mu);
+    __syncthreads();
+  };
+  // y += S(sigma)^{-1} r (FP32 factors), then r = w - S(mu) y in FP64; returns |r|^2 / |w|^2
+  auto refine = [&](double mu) {
+    for (int q = threadIdx.x; q < N; q += blockDim.x) r32[q] = (float)r[q];
+    __syncthreads();
+    band_solve_shfl(Lb, bw1, invD, r32, N, bw);
+    for (int q = threadIdx.x; q < N; q += blockDim.x) y[q] += (double)r32[q];
+    __syncthreads();
+    double v[2] = {0.0, 0.0};
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      const double rq = resid_row(y, q, mu);
+      r[q] = rq;
+      v[0] += rq * rq;
+      v[1] += wv[q] * wv[q];
+    }
+    block_sum<2>(v, scratch, red);
+    return red[1] > 0.0 ? red[0] / red[1] : 0.0;
+  };
+  // refine to rel^2 <= target; false if the iteration stalls first (then refactor at mu)
+  auto solve = [&](double mu, double target) {
+    start(mu);
+    double prev = INFINITY;
+    for (int k = 0; k < 16; ++k) {
+      const double rel = refine(mu);
+      if (rel <= target) return true;
+      if (!(rel < 0.1 * prev)) return false;
+      prev = rel;
+    }
+    return false;
+  };
+  auto eval = [&](double mu, double& f, double& fp) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      v[0] += wv[q] * y[q];
+      v[1] += y[q] * r[q];
+      v[2] += gb[q] * y[q];
+      v[3] += y[q] * band_mv(MH, y, q);
+    }
+    block_sum<4>(v, scratch, red);
+    f = alpha - mu * beta - (red[0] + red[1]);
+    fp = -beta + 2.0 * red[2] - red[3];
+  };
+  // squared relative residuals: Newton steps need y to ~1e-6 (the variational f then has a
+  // relative error ~1e-12); the eigenvector is refined until the FP64 residual stops falling
+  const double kNewtonTarget = 1e-12, kFinalTarget = 1e-30;
+  double mu = alpha / beta, lo = 0.0, hi = INFINITY, lam = NAN;
+  int it = 0, status = 0;
+  bool have = false, factored = false;
+  for (; it < a.max_iter; ++it) {
+    bool ok = factored && solve(mu, kNewtonTarget);
+    if (!ok) {
+      if (!factor(mu)) {
+        factored = false;
+        hi = mu;
+        mu = 0.5 * (lo + hi);
+        have = false;
+        continue;
+      }
+      factored = true;
+      solve(mu, kNewtonTarget);
+    }
+    have = true;
+    double f, fp;
+    eval(mu, f, fp);
+    if (f > 0.0) lo = mu;
+    else hi = mu;
+    const double step = (fp < 0.0) ? -f / fp : 0.0;
+    if (fp < 0.0 && fabs(step) <= 1e-9 * fabs(mu)) {
+      lam = mu + step;
+      break;
+    }
+    double nmu = (fp < 0.0) ? mu + step : 0.5 * (lo + hi);
+    if (!(nmu > lo && nmu < hi)) nmu = isfinite(hi) ? 0.5 * (lo + hi) : 2.0 * mu;
+    if (isfinite(hi) && hi - lo <= 1e-15 * hi) {
+      lam = mu;
+      break;
+    }
+    mu = nmu;
+  }
+  if (it >= a.max_iter) status |= MLEV_ST_RR_NOCONV;
+  if (!(lam == lam)) lam = mu;
+  if (!have) {
+    if (factor(mu)) {
+      factored = true;
+      have = true;
+    } else {
+      status |= MLEV_ST_RR_BREAKDOWN;
+    }
+  }
+  // y = S(mu)^{-1} w to the FP64 floor for the eigenvector; a stall with factors taken at
+  // another shift refactors once (a stall at the same shift is the rounding floor)
+  if (have && !solve(mu, kFinalTarget) && sig != mu && factor(mu)) solve(mu, kFinalTarget);
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    v[0] += y[q] * band_mv(MH, y, q);
+    v[1] += gb[q] * y[q];
+    v[2] += y[q];
+  }
+  block_sum<3>(v, scratch, red);
+  const double bn = red[0] - 2.0 * red[1] + beta;
+  const double S = (double)(1LL << (2 * a.L));
+  const double integral = sigma - S * red[2];
+  const double sc = (integral >= 0 ? 1.0 : -1.0) / sqrt(bn);
+  const int ncoef = (ncx + 1) * (ncy + 1);
+  double* cp = a.c + (long long)p * ncoef;
+  for (int q = threadIdx.x; q < ncoef; q += blockDim.x) cp[q] = 0.0;
+  __syncthreads();
+  for (int q = threadIdx.x; q < N; q += blockDim.x) {
+    const int X = q % (ncx - 1) + 1, Y = q / (ncx - 1) + 1;
+    cp[Y * (ncx + 1) + X] = is_free(G, 0, ncx, ncy, X, Y) ? -sc * y[q] : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    a.c0[p] = sc;
+    a.lam[p * (a.n + 1) + a.L] = lam;
+    a.stat[p * a.stat_stride + MLEV_STAT_RR_IT + a.L] = it + 1;
+    if (!isfinite(lam) || !isfinite(sc)) status |= MLEV_ST_NONFINITE;
+    if (status) atomicOr((unsigned long long*)&a.stat[p * a.stat_stride + MLEV_STAT_FLAGS], (unsigned long long)status);
+  }
+}
+
+// Shared memory of k_rr_mixed: 5 FP64 vectors, K_H, M_H and S(mu), the FP32 band, 2 FP32
+// vectors and the pair table.
+size_t rr_mixed_smem_bytes(int nhb, int bw) {
+  return (size_t)nhb * 5 * 8 + 3 * (size_t)nhb * (bw + 1) * 8 + ((size_t)nhb * (bw + 1) + 2 * (size_t)nhb + 2) * 4 +
+         (size_t)(bw * (bw + 1) / 2) * 4 + 16;
+}
+// The mixed kernel keeps one factorisation pair per thread (bw (bw + 1) / 2 <= 256) and the
+// warp solve's window in one warp's lanes (bw <= 31); wider coarse grids use the FP64 kernel.
+int rr_mixed_supported(int nhb, int bw) { return bw * (bw + 1) / 2 <= 256 && bw <= 31 && nhb > 0; }
+
 // Shared memory of the Rayleigh-Ritz kernel when its band system is kept on chip.
 size_t rr_smem_bytes(int nhb, int bw) {
   return ((size_t)nhb * (bw + 1) + 5 * (size_t)nhb) * 8 + (size_t)(bw * (bw + 1) / 2) * 4;
@@ -445,9 +1060,16 @@ void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, kRRSmemMax);
+    cudaFuncSetAttribute(k_rr_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, kRRSmemMax);
     attr = true;
   }
-  const size_t smem = a.smem ? rr_smem_bytes(a.nhb, a.bw) : (size_t)(a.bw * (a.bw + 1) / 2) * 4;
+  const size_t pairs_only = (size_t)(a.bw * (a.bw + 1) / 2) * 4;
+  if (a.mixed) {
+    const size_t smem = a.smem ? rr_mixed_smem_bytes(a.nhb, a.bw) : pairs_only;
+    k_rr_mixed<<<a.B, 256, smem, s>>>(G, a);
+    return;
+  }
+  const size_t smem = a.smem ? rr_smem_bytes(a.nhb, a.bw) : pairs_only;
   k_rr<<<a.B, 256, smem, s>>>(G, a);
 }
 

@@ -102,6 +102,11 @@ struct Level1Args {
 };
 template <typename T>
 void launch_level1(const DevGeom& G, const GlobalLayout& gl, const Level1Args& a, cudaStream_t s);
+// on-chip variant: every vector and grid of the level-1 hierarchy in shared memory
+constexpr int kL1SmemMax = 200 * 1024;
+size_t level1_smem_bytes(long long nn0, long long tot, int tsize);
+template <typename T>
+void launch_level1_sm(const DevGeom& G, const GlobalLayout& gl, const Level1Args& a, size_t smem, cudaStream_t s);
 
 struct RRArgs {
   int B, L, n;
@@ -117,9 +122,12 @@ struct RRArgs {
   long long* stat;
   int stat_stride;
   int max_iter;
+  int mixed;             // 1: FP32 band factors with FP64 refinement (k_rr_mixed)
 };
 void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s);
 size_t rr_smem_bytes(int nhb, int bw);
+size_t rr_mixed_smem_bytes(int nhb, int bw);
+int rr_mixed_supported(int nhb, int bw);
 constexpr int kRRSmemMax = 200 * 1024;
 
 // ---- adjoint of Algorithm 4.2 (kern_adj.cu) ----

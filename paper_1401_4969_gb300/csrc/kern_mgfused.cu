@@ -13,6 +13,7 @@
 //   down to the coarsest solve and back) on copies of those grids in shared memory.
 #include "kern_blk.cuh"
 #include "kern_launch.h"
+#include "kern_tail.cuh"
 
 namespace mlev {
 
@@ -236,108 +237,6 @@ __global__ void __launch_bounds__(256) k_mg_up(DevGeom G, const Tile* __restrict
       const int i = t.x0 + aa, j = t.y0 + bb, q = (bb + MLEV_TMA_FOY) * SW + aa + MLEV_TMA_FOX;
       if (i <= g.nx && j <= g.ny && uk[q]) X[g.off + (long long)j * g.pitch + i] = xs[q];
     }
-}
-
-constexpr int kTailMaxLev = 16;
-
-// Shared-memory grid of the tail: compact row pitch W = nx + 1, x / f values and a mask of
-// the unknowns; `g` is the job's original descriptor (coordinates, level, coefficient).
-template <typename T>
-struct SmGrid {
-  T* x;
-  T* f;
-  uint8_t* m;
-  int nx, ny, W;
-  const GridDesc* g;
-};
-
-// Red-black sweeps with a 32 x 16 thread block: thread (tx, ty) visits rows ty + 1, ty + 17,
-// ... and, in each row, the nodes of the current colour with stride 64.
-template <typename T, int KK>
-__device__ void tail_smooth(const DevGeom& G, const SmGrid<T>& s, int sweeps, bool reverse, T omega) {
-  const GridDesc& g = *s.g;
-  for (int it = 0; it < sweeps; ++it)
-    for (int cc = 0; cc < 2; ++cc) {
-      const int color = reverse ? 1 - cc : cc;
-      for (int j = 1 + threadIdx.y; j < s.ny; j += blockDim.y) {
-        const int i0 = ((color + j) & 1) ? 1 : 2;
-        for (int i = i0 + 2 * threadIdx.x; i < s.nx; i += 2 * blockDim.x) {
-          const int q = j * s.W + i;
-          if (!s.m[q]) continue;
-          const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
-          const T v = s.f[q] + (T)w.e * s.x[q + 1] + (T)w.w * s.x[q - 1] + (T)w.n * s.x[q + s.W] +
-                      (T)w.s * s.x[q - s.W];
-          s.x[q] += omega * (v / (T)(w.e + w.w + w.n + w.s) - s.x[q]);
-        }
-      }
-      __syncthreads();
-    }
-}
-
-template <typename T, int KK>
-__device__ __forceinline__ T tail_res(const DevGeom& G, const SmGrid<T>& s, int i, int j) {
-  const int q = j * s.W + i;
-  if (!s.m[q]) return (T)0;
-  const GridDesc& g = *s.g;
-  const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
-  return s.f[q] - ((T)(w.e + w.w + w.n + w.s) * s.x[q] - (T)w.e * s.x[q + 1] - (T)w.w * s.x[q - 1] -
-                   (T)w.n * s.x[q + s.W] - (T)w.s * s.x[q - s.W]);
-}
-
-template <typename T, int KK>
-__device__ void tail_restrict(const DevGeom& G, const SmGrid<T>& fi, const SmGrid<T>& co) {
-  for (int J = threadIdx.y; J <= co.ny; J += blockDim.y)
-    for (int I = threadIdx.x; I <= co.nx; I += blockDim.x) {
-      const int q = J * co.W + I;
-      co.x[q] = (T)0;
-      if (!co.m[q]) continue;
-      const int i = 2 * I, j = 2 * J;
-      const T half = tail_res<T, KK>(G, fi, i + 1, j) + tail_res<T, KK>(G, fi, i - 1, j) +
-                     tail_res<T, KK>(G, fi, i, j + 1) + tail_res<T, KK>(G, fi, i, j - 1) +
-                     tail_res<T, KK>(G, fi, i + 1, j + 1) + tail_res<T, KK>(G, fi, i - 1, j - 1);
-      co.f[q] = tail_res<T, KK>(G, fi, i, j) + (T)0.5 * half;
-    }
-  __syncthreads();
-}
-
-template <typename T>
-__device__ void tail_prolong(const SmGrid<T>& fi, const SmGrid<T>& co) {
-  for (int j = 1 + threadIdx.y; j < fi.ny; j += blockDim.y)
-    for (int i = 1 + threadIdx.x; i < fi.nx; i += blockDim.x) {
-      const int q = j * fi.W + i;
-      if (!fi.m[q]) continue;
-      const int I = i >> 1, J = j >> 1, c = J * co.W + I;
-      T v;
-      if (!(i & 1) && !(j & 1)) v = co.x[c];
-      else if ((i & 1) && !(j & 1)) v = (T)0.5 * (co.x[c] + co.x[c + 1]);
-      else if (!(i & 1) && (j & 1)) v = (T)0.5 * (co.x[c] + co.x[c + co.W]);
-      else v = (T)0.5 * (co.x[c] + co.x[c + co.W + 1]);
-      fi.x[q] += v;
-    }
-  __syncthreads();
-}
-
-template <typename T>
-__device__ void tail_direct(const SmGrid<T>& s, const T* __restrict__ inv, T* fbuf) {
-  const int nx1 = s.nx - 1, nd = nx1 * (s.ny - 1);
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
-  for (int r = tid; r < nd; r += nt) {
-    const int j = r / nx1 + 1, i = r - (j - 1) * nx1 + 1, q = j * s.W + i;
-    fbuf[r] = s.m[q] ? s.f[q] : (T)0;
-  }
-  __syncthreads();
-  // one warp per row of the inverse: coalesced loads, shuffle reduction
-  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  for (int r = warp; r < nd; r += nw) {
-    T acc = (T)0;
-    for (int c = lane; c < nd; c += 32) acc += inv[r * nd + c] * fbuf[c];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const int j = r / nx1 + 1, i = r - (j - 1) * nx1 + 1, q = j * s.W + i;
-      s.x[q] = s.m[q] ? acc : (T)0;
-    }
-  }
-  __syncthreads();
 }
 
 // tiles[b].grid = the job's grid at the first tail depth; its coarser grids follow it.
