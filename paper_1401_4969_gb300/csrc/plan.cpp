@@ -194,7 +194,6 @@ std::string Plan::build(const mlev_opts& o) {
   for (int j = 0; j < m; ++j) nd_max = std::max(nd_max, (Om[j][2] - Om[j][0] - 1) * (Om[j][3] - Om[j][1] - 1));
   nd_max = std::max(nd_max, 1);
   sub_direct = nd_max <= kDirectMax;
-  strip_coarse_nodes = (4 * ncx + 1) * (4 * ncy + 1);
 
   // ---- region grids ----
   regions.clear();
@@ -218,8 +217,24 @@ std::string Plan::build(const mlev_opts& o) {
     sub_roff[j] = add_region(reg);
     sub_full[j] = full;
   }
+  // G_{m+1} region: quarter cells (level 2) with label 0; when it is a union of level-1 cells
+  // (delta a multiple of H/2) the strip hierarchy coarsens one level further, to T_{h_1}
   std::vector<uint8_t> sreg(qlabel.size());
   for (size_t i = 0; i < qlabel.size(); ++i) sreg[i] = qlabel[i] == 0;
+  strip_lvl = 1;
+  for (int y = 0; y < 2 * ncy && strip_lvl == 1; ++y)
+    for (int x = 0; x < 2 * ncx && strip_lvl == 1; ++x) {
+      const int q = (2 * y) * (4 * ncx) + 2 * x;
+      const uint8_t v = sreg[q];
+      if (sreg[q + 1] != v || sreg[q + 4 * ncx] != v || sreg[q + 4 * ncx + 1] != v) strip_lvl = 2;
+    }
+  if (strip_lvl == 1) {
+    std::vector<uint8_t> s1((size_t)4 * ncx * ncy);
+    for (int y = 0; y < 2 * ncy; ++y)
+      for (int x = 0; x < 2 * ncx; ++x) s1[y * 2 * ncx + x] = sreg[(2 * y) * (4 * ncx) + 2 * x];
+    sreg.swap(s1);
+  }
+  strip_coarse_nodes = ((ncx << strip_lvl) + 1) * ((ncy << strip_lvl) + 1);
   const long long strip_roff = add_region(sreg);
   std::vector<uint8_t> l1reg;
   {
@@ -252,7 +267,8 @@ std::string Plan::build(const mlev_opts& o) {
     LevelPlan& P = lp[L];
     P.grid_begin = (int)grids.size();
     long long pool = 0, pool64 = 0;
-    std::vector<std::vector<int>> sub_by_depth(L + 1), strip_by_depth(L - 1);
+    const int sdmax = L - strip_lvl;  // strip depths 0 .. sdmax (coarsest grid on level strip_lvl)
+    std::vector<std::vector<int>> sub_by_depth(L + 1), strip_by_depth(sdmax + 1);
     std::vector<int> sub_coarse, sub_topg, strip_coarse;
     P.sub_top_off = (int)sub_top.size();
     sub_top.resize(sub_top.size() + (size_t)B * m);
@@ -295,7 +311,7 @@ std::string Plan::build(const mlev_opts& o) {
           if (dpt == L) sub_coarse.push_back(gi);
         }
       }
-      for (int dpt = 0; dpt <= L - 2; ++dpt) {
+      for (int dpt = 0; dpt <= sdmax; ++dpt) {
         int l = L - dpt;
         GridDesc g{};
         g.nx = ncx << l;
@@ -306,9 +322,9 @@ std::string Plan::build(const mlev_opts& o) {
         g.level = l;
         g.problem = b;
         g.full = 0;
-        g.rshift = l - 2;
-        g.rnx = 4 * ncx;
-        g.rny = 4 * ncy;
+        g.rshift = l - strip_lvl;
+        g.rnx = ncx << strip_lvl;
+        g.rny = ncy << strip_lvl;
         g.job = B * m + b;
         g.depth = dpt;
         g.roff = strip_roff;
@@ -323,7 +339,7 @@ std::string Plan::build(const mlev_opts& o) {
         int gi = (int)grids.size();
         grids.push_back(g);
         strip_by_depth[dpt].push_back(gi);
-        if (dpt == L - 2) strip_coarse.push_back(gi);
+        if (dpt == sdmax) strip_coarse.push_back(gi);
       }
     }
     P.grid_end = (int)grids.size();
@@ -336,8 +352,8 @@ std::string Plan::build(const mlev_opts& o) {
       }
       P.sub[dpt].count = (int)((long long)tiles.size() - P.sub[dpt].off);
     }
-    P.strip.resize(L - 1);
-    for (int dpt = 0; dpt <= L - 2; ++dpt) {
+    P.strip.resize(sdmax + 1);
+    for (int dpt = 0; dpt <= sdmax; ++dpt) {
       P.strip[dpt].off = (long long)tiles.size();
       for (int gi : strip_by_depth[dpt]) {
         add_tiles_for(gi);

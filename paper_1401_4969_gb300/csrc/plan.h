@@ -84,7 +84,8 @@ struct Plan {
   int nhb = 0, bw = 0;                     // coarse band system: rows (ncx-1)(ncy-1), half bandwidth
   int sub_direct = 0;                      // subdomain coarsest grids solved by a dense inverse
   int nd_max = 0;                          // largest coarsest-window size (interior nodes) of a subdomain
-  int strip_coarse_nodes = 0;              // nodes of the strip's coarsest (T_{h_2}) grid
+  int strip_lvl = 2;                       // level of the strip's coarsest grid (1 if G_{m+1} is a union of T_{h_1} cells)
+  int strip_coarse_nodes = 0;              // nodes of the strip's coarsest grid
   int n_tmap_grids = 0;                    // grids carrying TMA tensor maps (3 maps each)
 
   // ---- workspace layout (depends on opts) ----
