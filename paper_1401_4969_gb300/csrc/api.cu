@@ -287,8 +287,12 @@ struct Launcher {
     G.H = P.H;
     G.kap = P.kap_template;
     double* klvl = at<double>(ws, P.w_klvl);
+    float* klvl_f = at<float>(ws, P.w_klvl_f);
+    float* kcf = at<float>(ws, P.w_kcf);
     G.kap.lvl = klvl;
+    G.kap.lvl_f = klvl_f;
     G.kap.coarse = P.kappa_kind == MLEV_KAPPA_PER_COARSE_CELL ? kappa_src : nullptr;
+    G.kap.coarse_f = P.kappa_kind == MLEV_KAPPA_PER_COARSE_CELL ? kcf : nullptr;
     (void)cudaGetLastError();  // do not attribute an earlier unrelated failure to this solve
     long long* stat = at<long long>(ws, P.w_stat);
     const int stat_stride = mlev_stat_stride(n);
@@ -297,13 +301,16 @@ struct Launcher {
     count = 0;
     // ---- coefficient on every level, coarse pencil
     if (P.kappa_kind == MLEV_KAPPA_PER_FINE_ELEM) {
-      go(F_KAPPA, 16.0 * B * P.lvl_nx(n) * P.lvl_ny(n) * 2,
-         [&] { launch_kappa_copy_fine(G.kap, n, B, kappa_src, klvl, s); });
+      go(F_KAPPA, 20.0 * B * P.lvl_nx(n) * P.lvl_ny(n) * 2,
+         [&] { launch_kappa_copy_fine(G.kap, n, B, kappa_src, klvl, klvl_f, s); });
       for (int l = n - 1; l >= P.l1_lc; --l)
-        go(F_KAPPA, 40.0 * B * P.lvl_nx(l) * P.lvl_ny(l) * 2, [&] { launch_kappa_average(G.kap, l, B, klvl, s); });
+        go(F_KAPPA, 44.0 * B * P.lvl_nx(l) * P.lvl_ny(l) * 2,
+           [&] { launch_kappa_average(G.kap, l, B, klvl, klvl_f, s); });
     } else if (P.kappa_kind == MLEV_KAPPA_PER_COARSE_CELL) {
+      go(F_KAPPA, 12.0 * B * P.ncx * P.ncy, [&] { launch_kappa_to_f((long long)B * P.ncx * P.ncy, kappa_src, kcf, s); });
       for (int l = -1; l >= P.l1_lc; --l)
-        go(F_KAPPA, 40.0 * B * P.lvl_nx(l) * P.lvl_ny(l) * 2, [&] { launch_kappa_average(G.kap, l, B, klvl, s); });
+        go(F_KAPPA, 44.0 * B * P.lvl_nx(l) * P.lvl_ny(l) * 2,
+           [&] { launch_kappa_average(G.kap, l, B, klvl, klvl_f, s); });
     }
     double* KH = at<double>(ws, P.w_band);
     double* MH = KH + (size_t)B * P.nhb * (P.bw + 1);

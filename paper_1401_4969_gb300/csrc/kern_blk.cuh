@@ -19,7 +19,7 @@ __device__ void blk_smooth(const DevGeom& G, const GridDesc& g, T* X, const T* F
         const int j = q / W, i = q - j * W;
         if (((i + j) & 1) != color || !is_unknown(G, g, i, j)) continue;
         const long long c = (long long)j * g.pitch + i;
-        const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+        const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
         const T v = F[g.off + c] + (T)w.e * x[c + 1] + (T)w.w * x[c - 1] + (T)w.n * x[c + g.pitch] +
                     (T)w.s * x[c - g.pitch];
         x[c] += omega * (v / (T)(w.e + w.w + w.n + w.s) - x[c]);
@@ -32,7 +32,7 @@ template <typename T, int KK>
 __device__ __forceinline__ T blk_res(const DevGeom& G, const GridDesc& g, const T* X, const T* F, int i, int j) {
   if (!is_unknown(G, g, i, j)) return (T)0;
   const long long c = (long long)j * g.pitch + i;
-  const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+  const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
   return F[g.off + c] - apply_k<T, T>(X + g.off, c, g.pitch, w);
 }
 

@@ -100,9 +100,71 @@ __device__ __forceinline__ W4 edge_weights(const KappaDev& kv, int p, int l, int
   return r;
 }
 
-// (K x)_c with the given weights on a pitched array.
-template <typename T, typename V>
-__device__ __forceinline__ V apply_k(const T* x, long long c, int pitch, const W4& w) {
+// The same coefficient and edge weights in precision T: T = float reads the FP32 copies of
+// the coefficient tables, so FP32 multigrid kernels issue no FP64 arithmetic.
+template <typename T>
+struct EW {
+  T e, w, n, s;
+};
+
+template <typename T, int KK>
+__device__ __forceinline__ T kap_tri_t(const KappaDev& kv, int p, int l, int x, int y, int t) {
+  if (KK == MLEV_KAPPA_ONE) return (T)1;
+  const int nx = lvl_cells_x(kv, l), ny = lvl_cells_y(kv, l);
+  if (x < 0 || y < 0 || x >= nx || y >= ny) return (T)0;
+  if (KK == MLEV_KAPPA_PER_COARSE_CELL && l >= 0) {
+    const long long q = (long long)p * kv.ncx * kv.ncy + (y >> l) * kv.ncx + (x >> l);
+    if constexpr (sizeof(T) == 4) return kv.coarse_f[q];
+    else return kv.coarse[q];
+  }
+  const int i = l - MLEV_LMIN;
+  const long long q = kv.lvl_off[i] + (long long)p * kv.lvl_bstride[i] + ((long long)y * nx + x) * 2 + t;
+  if constexpr (sizeof(T) == 4) return kv.lvl_f[q];
+  else return kv.lvl[q];
+}
+
+template <typename T, int KK>
+__device__ __forceinline__ EW<T> edge_weights_t(const KappaDev& kv, int p, int l, int gi, int gj) {
+  EW<T> r;
+  if (KK == MLEV_KAPPA_ONE) {
+    r.e = r.w = r.n = r.s = (T)1;
+    return r;
+  }
+  if (KK == MLEV_KAPPA_PER_COARSE_CELL && l >= 0) {
+    const int ci = gi >> l, cw = (gi - 1) >> l, cj = gj >> l, cs = (gj - 1) >> l;
+    const long long b = (long long)p * kv.ncx * kv.ncy;
+    T kc_c, kc_s, kc_w, kc_sw;
+    if constexpr (sizeof(T) == 4) {
+      kc_c = kv.coarse_f[b + cj * kv.ncx + ci];
+      kc_s = kv.coarse_f[b + cs * kv.ncx + ci];
+      kc_w = kv.coarse_f[b + cj * kv.ncx + cw];
+      kc_sw = kv.coarse_f[b + cs * kv.ncx + cw];
+    } else {
+      kc_c = kv.coarse[b + cj * kv.ncx + ci];
+      kc_s = kv.coarse[b + cs * kv.ncx + ci];
+      kc_w = kv.coarse[b + cj * kv.ncx + cw];
+      kc_sw = kv.coarse[b + cs * kv.ncx + cw];
+    }
+    r.e = (T)0.5 * (kc_c + kc_s);
+    r.n = (T)0.5 * (kc_c + kc_w);
+    r.w = (T)0.5 * (kc_w + kc_sw);
+    r.s = (T)0.5 * (kc_s + kc_sw);
+    return r;
+  }
+  const T kLc = kap_tri_t<T, KK>(kv, p, l, gi, gj, 0), kUc = kap_tri_t<T, KK>(kv, p, l, gi, gj, 1);
+  const T kUs = kap_tri_t<T, KK>(kv, p, l, gi, gj - 1, 1);
+  const T kLw = kap_tri_t<T, KK>(kv, p, l, gi - 1, gj, 0);
+  const T kLsw = kap_tri_t<T, KK>(kv, p, l, gi - 1, gj - 1, 0), kUsw = kap_tri_t<T, KK>(kv, p, l, gi - 1, gj - 1, 1);
+  r.e = (T)0.5 * (kLc + kUs);
+  r.n = (T)0.5 * (kUc + kLw);
+  r.w = (T)0.5 * (kLw + kUsw);
+  r.s = (T)0.5 * (kUs + kLsw);
+  return r;
+}
+
+// (K x)_c with the given weights (W4 or EW<T>) on a pitched array.
+template <typename T, typename V, typename WW>
+__device__ __forceinline__ V apply_k(const T* x, long long c, int pitch, const WW& w) {
   return (V)(w.e + w.w + w.n + w.s) * (V)x[c] - (V)w.e * (V)x[c + 1] - (V)w.w * (V)x[c - 1] -
          (V)w.n * (V)x[c + pitch] - (V)w.s * (V)x[c - pitch];
 }

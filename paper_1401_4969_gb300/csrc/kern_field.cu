@@ -177,19 +177,27 @@ __global__ void __launch_bounds__(256) k_output_u(DevGeom G, GlobalLayout gl, in
   out[(long long)p * (nx + 1) * (ny + 1) + (long long)j * (nx + 1) + i] = v;
 }
 
-// Finest-level triangle values copied into the per-level table.
-__global__ void k_kappa_copy_fine(KappaDev kv, int n, int B, const double* src, double* lvl) {
+// Finest-level triangle values copied into the per-level table (and its FP32 copy).
+__global__ void k_kappa_copy_fine(KappaDev kv, int n, int B, const double* src, double* lvl, float* lvl_f) {
   const long long per = (long long)lvl_cells_x(kv, n) * lvl_cells_y(kv, n) * 2;
   const long long tot = per * B;
   const long long off = kv.lvl_off[lidx(n)];
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot; q += (long long)gridDim.x * blockDim.x)
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot; q += (long long)gridDim.x * blockDim.x) {
     lvl[off + q] = src[q];
+    lvl_f[off + q] = (float)src[q];
+  }
+}
+
+// FP32 copy of the per-coarse-cell coefficient.
+__global__ void k_kappa_to_f(long long tot, const double* src, float* dst) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot; q += (long long)gridDim.x * blockDim.x)
+    dst[q] = (float)src[q];
 }
 
 // Triangle values of level l as the mean of their four children on level l+1 (the
 // exact P1 stiffness of the coarser triangle; children as in regular refinement).
 template <int KK>
-__global__ void k_kappa_average(KappaDev kv, int l, int B, double* lvl) {
+__global__ void k_kappa_average(KappaDev kv, int l, int B, double* lvl, float* lvl_f) {
   const int nx = lvl_cells_x(kv, l), ny = lvl_cells_y(kv, l);
   const long long tot = (long long)nx * ny * B;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot; q += (long long)gridDim.x * blockDim.x) {
@@ -201,9 +209,11 @@ __global__ void k_kappa_average(KappaDev kv, int l, int B, double* lvl) {
                               kap_tri<KK>(kv, p, l + 1, X + 1, Y + 1, 0) + kap_tri<KK>(kv, p, l + 1, X + 1, Y, 1));
     const double up = 0.25 * (kap_tri<KK>(kv, p, l + 1, X, Y, 1) + kap_tri<KK>(kv, p, l + 1, X + 1, Y + 1, 1) +
                               kap_tri<KK>(kv, p, l + 1, X, Y + 1, 1) + kap_tri<KK>(kv, p, l + 1, X, Y + 1, 0));
-    double* dst = lvl + kv.lvl_off[lidx(l)] + (long long)p * kv.lvl_bstride[lidx(l)];
-    dst[(long long)r * 2 + 0] = lo;
-    dst[(long long)r * 2 + 1] = up;
+    const long long o = kv.lvl_off[lidx(l)] + (long long)p * kv.lvl_bstride[lidx(l)] + (long long)r * 2;
+    lvl[o] = lo;
+    lvl[o + 1] = up;
+    lvl_f[o] = (float)lo;
+    lvl_f[o + 1] = (float)up;
   }
 }
 
@@ -296,11 +306,15 @@ void launch_output_u(const DevGeom& G, const GlobalLayout& gl, int L, int B, con
                      const double* c0, double* u_out, cudaStream_t s) {
   k_output_u<<<global_grid(gl, L, B), dim3(GX, GY), 0, s>>>(G, gl, L, ut, c, c0, u_out);
 }
-void launch_kappa_copy_fine(const KappaDev& kv, int n, int B, const double* src, double* lvl, cudaStream_t s) {
-  k_kappa_copy_fine<<<1024, 256, 0, s>>>(kv, n, B, src, lvl);
+void launch_kappa_copy_fine(const KappaDev& kv, int n, int B, const double* src, double* lvl, float* lvl_f,
+                            cudaStream_t s) {
+  k_kappa_copy_fine<<<1024, 256, 0, s>>>(kv, n, B, src, lvl, lvl_f);
 }
-void launch_kappa_average(const KappaDev& kv, int l, int B, double* lvl, cudaStream_t s) {
-  MLEV_DISPATCH_KK(kv.kind, (k_kappa_average<KK><<<1024, 256, 0, s>>>(kv, l, B, lvl)));
+void launch_kappa_to_f(long long count, const double* src, float* dst, cudaStream_t s) {
+  k_kappa_to_f<<<256, 256, 0, s>>>(count, src, dst);
+}
+void launch_kappa_average(const KappaDev& kv, int l, int B, double* lvl, float* lvl_f, cudaStream_t s) {
+  MLEV_DISPATCH_KK(kv.kind, (k_kappa_average<KK><<<1024, 256, 0, s>>>(kv, l, B, lvl, lvl_f)));
 }
 void launch_band_setup(const DevGeom& G, int B, int nhb, int bw, double* KH, double* MH, cudaStream_t s) {
   const int n = nhb * B;

@@ -75,8 +75,10 @@ void launch_strip_update(const DevGeom& G, const GlobalLayout& gl, const LevelAr
 void launch_aug(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, double* partials, cudaStream_t s);
 void launch_output_u(const DevGeom& G, const GlobalLayout& gl, int L, int B, const double* ut, const double* c,
                      const double* c0, double* u_out, cudaStream_t s);
-void launch_kappa_copy_fine(const KappaDev& kv, int n, int B, const double* src, double* lvl, cudaStream_t s);
-void launch_kappa_average(const KappaDev& kv, int l, int B, double* lvl, cudaStream_t s);
+void launch_kappa_copy_fine(const KappaDev& kv, int n, int B, const double* src, double* lvl, float* lvl_f,
+                            cudaStream_t s);
+void launch_kappa_to_f(long long count, const double* src, float* dst, cudaStream_t s);
+void launch_kappa_average(const KappaDev& kv, int l, int B, double* lvl, float* lvl_f, cudaStream_t s);
 void launch_band_setup(const DevGeom& G, int B, int nhb, int bw, double* KH, double* MH, cudaStream_t s);
 void launch_lambda_out(int B, int n, const double* lam, double* out, cudaStream_t s);
 

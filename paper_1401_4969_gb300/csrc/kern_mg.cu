@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) k_smooth(DevGeom G, const Tile* __restric
   if (((i + j) & 1) != color || !is_unknown(G, g, i, j)) return;
   T* x = X + g.off;
   const long long c = (long long)j * g.pitch + i;
-  const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+  const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
   const T s = F[g.off + c] + (T)w.e * x[c + 1] + (T)w.w * x[c - 1] + (T)w.n * x[c + g.pitch] + (T)w.s * x[c - g.pitch];
   x[c] += omega * (s / (T)(w.e + w.w + w.n + w.s) - x[c]);
 }
@@ -36,7 +36,7 @@ template <typename T, int KK>
 __device__ __forceinline__ T residual_at(const DevGeom& G, const GridDesc& g, const T* X, const T* F, int i, int j) {
   if (!is_unknown(G, g, i, j)) return (T)0;
   const long long c = (long long)j * g.pitch + i;
-  const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+  const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
   return F[g.off + c] - apply_k<T, T>(X + g.off, c, g.pitch, w);
 }
 
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(256) k_coarsest(DevGeom G, const Tile* __restr
         const int i = q % (g.nx + 1), j = q / (g.nx + 1);
         if (((i + j) & 1) != color || !is_unknown(G, g, i, j)) continue;
         const long long c = (long long)j * g.pitch + i;
-        const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+        const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
         const T v = F[g.off + c] + (T)w.e * x[c + 1] + (T)w.w * x[c - 1] + (T)w.n * x[c + g.pitch] +
                     (T)w.s * x[c - g.pitch];
         x[c] += omega * (v / (T)(w.e + w.w + w.n + w.s) - x[c]);
@@ -198,9 +198,9 @@ __global__ void __launch_bounds__(1024) k_coarsest_smem(DevGeom G, const Tile* _
       const long long c = (long long)j * g.pitch + i;
       x[q] = X[g.off + c];
       if (is_unknown(G, g, i, j)) {
-        const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+        const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
         f[q] = F[g.off + c];
-        idg[q] = (T)(1.0 / (w.e + w.w + w.n + w.s));
+        idg[q] = (T)1 / (w.e + w.w + w.n + w.s);
         if (!kOne) {
           we[q] = (T)w.e; ww[q] = (T)w.w; wn[q] = (T)w.n; wsx[q] = (T)w.s;
         }

@@ -78,7 +78,7 @@ __device__ __forceinline__ void tile_half_sweep(const DevGeom& G, const GridDesc
     for (int a = a0 + 2 * threadIdx.x; a <= hi; a += 2 * blockDim.x) {
       const int q = (b + oy) * SW + a + ox;
       if (!uk[q]) continue;
-      const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + rx0 + a, g.oy + ry0 + b);
+      const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + rx0 + a, g.oy + ry0 + b);
       const T v = fs[q] + (T)w.e * xs[q + 1] + (T)w.w * xs[q - 1] + (T)w.n * xs[q + SW] + (T)w.s * xs[q - SW];
       xs[q] += omega * (v / (T)(w.e + w.w + w.n + w.s) - xs[q]);
     }
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_mg_down(DevGeom G, const Tile* __restri
           fs[q] = (T)0;
           continue;
         }
-        const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + rx0 + a, g.oy + ry0 + b);
+        const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + rx0 + a, g.oy + ry0 + b);
         fs[q] -= (T)(w.e + w.w + w.n + w.s) * xs[q] - (T)w.e * xs[q + 1] - (T)w.w * xs[q - 1] -
                  (T)w.n * xs[q + SW] - (T)w.s * xs[q - SW];
       }

@@ -32,7 +32,7 @@ __device__ void tail_smooth(const DevGeom& G, const SmGrid<T>& s, int sweeps, bo
         for (int i = i0 + 2 * threadIdx.x; i < s.nx; i += 2 * blockDim.x) {
           const int q = j * s.W + i;
           if (!s.m[q]) continue;
-          const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+          const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
           const T v = s.f[q] + (T)w.e * s.x[q + 1] + (T)w.w * s.x[q - 1] + (T)w.n * s.x[q + s.W] +
                       (T)w.s * s.x[q - s.W];
           s.x[q] += omega * (v / (T)(w.e + w.w + w.n + w.s) - s.x[q]);
@@ -47,7 +47,7 @@ __device__ __forceinline__ T tail_res(const DevGeom& G, const SmGrid<T>& s, int 
   const int q = j * s.W + i;
   if (!s.m[q]) return (T)0;
   const GridDesc& g = *s.g;
-  const W4 w = edge_weights<KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+  const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
   return s.f[q] - ((T)(w.e + w.w + w.n + w.s) * s.x[q] - (T)w.e * s.x[q + 1] - (T)w.w * s.x[q - 1] -
                    (T)w.n * s.x[q + s.W] - (T)w.s * s.x[q - s.W]);
 }

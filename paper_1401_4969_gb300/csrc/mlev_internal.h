@@ -54,6 +54,8 @@ struct KappaDev {
   int ncx, ncy;                      // T_H
   const double* coarse;              // kind PER_COARSE_CELL: [B][ncy][ncx]
   const double* lvl;                 // per-level triangle values (kinds 1 with level<0, and 2)
+  const float* coarse_f;             // FP32 copies of coarse and lvl, read by the FP32 multigrid
+  const float* lvl_f;
   long long lvl_off[MLEV_MAX_TOTAL_LEVELS];     // element offset of level (l - MLEV_LMIN)
   long long lvl_bstride[MLEV_MAX_TOTAL_LEVELS]; // elements per batch member at that level
 };

@@ -508,6 +508,8 @@ std::string Plan::build(const mlev_opts& o) {
     if (need) klv += (long long)B * lvl_nx(l) * lvl_ny(l) * 2;
   }
   take(w_klvl, (size_t)std::max<long long>(klv, 1) * 8);
+  take(w_klvl_f, (size_t)std::max<long long>(klv, 1) * 4);  // FP32 copies for the FP32 multigrid
+  take(w_kcf, kappa_kind == MLEV_KAPPA_PER_COARSE_CELL ? (size_t)B * ncx * ncy * 4 : 0);
   take(w_band, (size_t)2 * B * nhb * (bw + 1) * 8);
   const size_t gbytes = (size_t)B * glay.bstride * 8;
   take(w_ut[0], gbytes);
