@@ -444,6 +444,8 @@ struct Launcher {
       rr.lam = lam;
       rr.c = cL(L);
       rr.c0 = c0L(L);
+      rr.c_prev = cL(L - 1);
+      rr.c0_prev = c0L(L - 1);
       rr.stat = stat;
       rr.stat_stride = stat_stride;
       rr.max_iter = o.rr_max_iter;

@@ -375,33 +375,41 @@ template void launch_level1<float>(const DevGeom&, const GlobalLayout&, const Le
 template void launch_level1<double>(const DevGeom&, const GlobalLayout&, const Level1Args&, cudaStream_t);
 
 // ---------------------------------------------------------------- level-1 LOBPCG on chip
-// The same iteration as k_level1 with every vector and the whole level-1 multigrid
-// hierarchy in shared memory (compact row pitch nx + 1); used when they fit.
-// Layout: 10 FP64 vectors of the level-1 grid, then x (T) of every level, f (T) of every
-// level, then the unknown masks.
+// The iteration of k_level1 with every vector and the whole level-1 multigrid hierarchy in
+// shared memory (compact row pitch nx + 1), used when they fit, and with the small Ritz
+// step kept off the FP64 pipe: x, K x, M x and the residual r are FP64 (K x and M x are
+// recomputed from x every iteration, so the residual test is exact), while the search
+// directions w (one V-cycle on r) and p, their images and the 3 x 3 Rayleigh-Ritz pencil
+// are FP32. The pencil is formed shifted by the FP64 Rayleigh quotient rho of x:
+// (A - rho B)_{xw} = r^T w and (A - rho B)_{xx} = 0, so FP32 resolves the small
+// coefficients of w and p; an FP32 coefficient error only makes a step slightly
+// suboptimal. Layout: FP32 Gram partials [11][threads], 4 FP64 vectors, 6 FP32 vectors,
+// then x (T) and f (T) of every level and the unknown masks.
 template <typename T, int KK>
 __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, Level1Args a) {
   extern __shared__ __align__(16) unsigned char l1_raw[];
   __shared__ SmGrid<T> lv[kTailMaxLev];
-  __shared__ double scratch[16 * 12];
-  __shared__ double red[12];
-  __shared__ double sh_coef[4];
+  __shared__ double scratch[16 * 4];
+  __shared__ double red[4];
+  __shared__ float gram[12];
+  __shared__ float sh_coef[4];
   __shared__ int sh_flag;
   const int p = blockIdx.x, g0 = a.grid_begin + p * a.nlev, nlev = a.nlev;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
   const GridDesc& g = G.grids[g0];
   const int nx = g.nx, ny = g.ny, W = nx + 1, nn = W * (ny + 1);
-  double* G12 = reinterpret_cast<double*>(l1_raw);  // [12][threads] Gram partial sums
-  double* X = G12 + 12 * nt;
-  double *Wv = X + nn, *P = Wv + nn, *KX = P + nn, *MX = KX + nn, *KW = MX + nn, *MW = KW + nn, *KP = MW + nn,
-         *MP = KP + nn, *R = MP + nn;
+  float* G11 = reinterpret_cast<float*>(l1_raw);   // [11][nt]
+  double* X = reinterpret_cast<double*>(G11 + 12 * nt);
+  double *KX = X + nn, *MX = KX + nn, *R = MX + nn;
+  float* Wv = reinterpret_cast<float*>(R + nn);
+  float *KW = Wv + nn, *MW = KW + nn, *P = MW + nn, *KP = P + nn, *MP = KP + nn;
   if (tid == 0) {
     long long tot = 0;
     for (int k = 0; k < nlev; ++k) {
       const GridDesc& gk = G.grids[g0 + k];
       tot += ((long long)(gk.nx + 1) * (gk.ny + 1) + 1) & ~1LL;
     }
-    T* xb = reinterpret_cast<T*>(R + nn);
+    T* xb = reinterpret_cast<T*>(MP + nn);  // 6 nn floats after an 8-byte aligned start: aligned for T
     T* fb = xb + tot;
     uint8_t* mb = reinterpret_cast<uint8_t*>(fb + tot);
     long long off = 0;
@@ -429,44 +437,34 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
   __syncthreads();
   const uint8_t* m0 = lv[0].m;
   const double h = level_h(G.H, 1), m12 = h * h / 12.0;
+  const float m12f = (float)m12;
 #define L1_FOR_NODES for (int j = threadIdx.y; j <= ny; j += blockDim.y) for (int i = threadIdx.x; i <= nx; i += blockDim.x)
-  auto apply_km = [&](const double* v, double* kv, double* mv) {
+  auto apply_km64 = [&]() {  // K x, M x in FP64
     L1_FOR_NODES {
       const int q = j * W + i;
       if (!m0[q]) {
-        kv[q] = 0.0;
-        mv[q] = 0.0;
+        KX[q] = 0.0;
+        MX[q] = 0.0;
         continue;
       }
       const W4 w = edge_weights<KK>(G.kap, p, 1, g.ox + i, g.oy + j);
-      kv[q] = (w.e + w.w + w.n + w.s) * v[q] - w.e * v[q + 1] - w.w * v[q - 1] - w.n * v[q + W] - w.s * v[q - W];
-      mv[q] = m12 * (6.0 * v[q] + v[q + 1] + v[q - 1] + v[q + W] + v[q - W] + v[q + W + 1] + v[q - W - 1]);
+      KX[q] = (w.e + w.w + w.n + w.s) * X[q] - w.e * X[q + 1] - w.w * X[q - 1] - w.n * X[q + W] - w.s * X[q - W];
+      MX[q] = m12 * (6.0 * X[q] + X[q + 1] + X[q - 1] + X[q + W] + X[q - W] + X[q + W + 1] + X[q - W - 1]);
     }
     __syncthreads();
   };
   L1_FOR_NODES {
     const int q = j * W + i;
     X[q] = m0[q] ? 1.0 : 0.0;
-    Wv[q] = P[q] = KP[q] = MP[q] = R[q] = 0.0;
+    Wv[q] = P[q] = KP[q] = MP[q] = 0.f;
   }
   __syncthreads();
-  apply_km(X, KX, MX);
-  double rho;
-  {
-    double v[2] = {0.0, 0.0};
-    L1_FOR_NODES {
-      const int q = j * W + i;
-      v[0] += X[q] * KX[q];
-      v[1] += X[q] * MX[q];
-    }
-    block_sum_2d<2>(v, scratch, red);
-    rho = red[0] / red[1];
-  }
+  apply_km64();
   bool have_p = false;
   int it = 0;
-  double res = 1.0;
+  double res = 1.0, rho = 0.0;
   for (; it < a.max_iter; ++it) {
-    if (it > 0) {  // FP64 Rayleigh quotient of the current x
+    {  // FP64 Rayleigh quotient of x
       double v[2] = {0.0, 0.0};
       L1_FOR_NODES {
         const int q = j * W + i;
@@ -507,89 +505,81 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
     }
     L1_FOR_NODES {
       const int q = j * W + i;
-      Wv[q] = (double)lv[0].x[q];
+      Wv[q] = (float)lv[0].x[q];
     }
     __syncthreads();
-    apply_km(Wv, KW, MW);
+    // K w, M w in FP32 and the FP32 Gram sums
     {
-      double v[12];
+      float v[11];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) v[k] = 0.0;
+      for (int k = 0; k < 11; ++k) v[k] = 0.f;
       L1_FOR_NODES {
         const int q = j * W + i;
-        const double x = X[q], w = Wv[q], pp = P[q];
-        v[0] += x * KX[q]; v[1] += x * KW[q]; v[2] += x * KP[q];
-        v[3] += w * KW[q]; v[4] += w * KP[q]; v[5] += pp * KP[q];
-        v[6] += x * MX[q]; v[7] += x * MW[q]; v[8] += x * MP[q];
-        v[9] += w * MW[q]; v[10] += w * MP[q]; v[11] += pp * MP[q];
+        float kw = 0.f, mw = 0.f;
+        if (m0[q]) {
+          const EW<float> w = edge_weights_t<float, KK>(G.kap, p, 1, g.ox + i, g.oy + j);
+          kw = (w.e + w.w + w.n + w.s) * Wv[q] - w.e * Wv[q + 1] - w.w * Wv[q - 1] - w.n * Wv[q + W] - w.s * Wv[q - W];
+          mw = m12f * (6.f * Wv[q] + Wv[q + 1] + Wv[q - 1] + Wv[q + W] + Wv[q - W] + Wv[q + W + 1] + Wv[q - W - 1]);
+        }
+        KW[q] = kw;
+        MW[q] = mw;
+        const float w = Wv[q], pp = P[q], r = (float)R[q], x = (float)X[q], mx = (float)MX[q];
+        v[0] += r * w;   v[1] += r * pp;   v[2] += w * kw;   v[3] += w * mw;
+        v[4] += w * KP[q]; v[5] += w * MP[q]; v[6] += pp * KP[q]; v[7] += pp * MP[q];
+        v[8] += x * mx;  v[9] += x * mw;   v[10] += x * MP[q];
       }
-      // transposed reduction: warp k sums entry k over all threads
 #pragma unroll
-      for (int k = 0; k < 12; ++k) G12[k * nt + tid] = v[k];
+      for (int k = 0; k < 11; ++k) G11[k * nt + tid] = v[k];
       __syncthreads();
       const int lane = tid & 31, warp = tid >> 5;
-      if (warp < 12) {
-        double s = 0.0;
-        for (int q = lane; q < nt; q += 32) s += G12[warp * nt + q];
+      if (warp < 11) {
+        float s = 0.f;
+        for (int q = lane; q < nt; q += 32) s += G11[warp * nt + q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp] = s;
+        if (lane == 0) gram[warp] = s;
       }
       __syncthreads();
     }
     if (tid == 0) {
-      // Ritz pair of the 3 x 3 pencil (A - rho B, B) in FP32: the shift by the FP64 Rayleigh
-      // quotient removes the common part, so FP32 resolves the small coefficients of w and
-      // p (a coefficient error only makes the step slightly suboptimal; rho itself is
-      // recomputed in FP64 from the vectors)
-      const double A[3][3] = {{red[0], red[1], red[2]}, {red[1], red[3], red[4]}, {red[2], red[4], red[5]}};
-      const double Bm[3][3] = {{red[6], red[7], red[8]}, {red[7], red[9], red[10]}, {red[8], red[10], red[11]}};
-      float As[3][3], Bs[3][3], ths, cfs[3];
-      for (int r2 = 0; r2 < 3; ++r2)
-        for (int c2 = 0; c2 < 3; ++c2) {
-          As[r2][c2] = (float)(A[r2][c2] - rho * Bm[r2][c2]);
-          Bs[r2][c2] = (float)Bm[r2][c2];
-        }
-      bool ok = have_p && small_geneig_t<float>(3, As, Bs, ths, cfs, 1e-12f);
-      if (!ok) ok = small_geneig_t<float>(2, As, Bs, ths, cfs, 1e-12f);
-      double th = rho + (double)ths, cf[3] = {cfs[0], cfs[1], cfs[2]};
-      // near-dependent x, w, p defeat the FP32 Gram factorization: FP64 as before
-      if (!ok && have_p) ok = small_geneig(3, A, Bm, th, cf);
-      if (!ok) ok = small_geneig(2, A, Bm, th, cf);
+      const float rf = (float)rho;
+      const float As[3][3] = {{0.f, gram[0], gram[1]},
+                              {gram[0], gram[2] - rf * gram[3], gram[4] - rf * gram[5]},
+                              {gram[1], gram[4] - rf * gram[5], gram[6] - rf * gram[7]}};
+      const float Bs[3][3] = {{gram[8], gram[9], gram[10]}, {gram[9], gram[3], gram[5]}, {gram[10], gram[5], gram[7]}};
+      float th, cf[3];
+      bool ok = have_p && small_geneig_t<float>(3, As, Bs, th, cf, 1e-12f);
+      if (!ok) ok = small_geneig_t<float>(2, As, Bs, th, cf, 1e-12f);
       if (!ok) {
-        th = rho;
-        cf[0] = 1.0;
-        cf[1] = cf[2] = 0.0;
+        cf[0] = 1.f;
+        cf[1] = cf[2] = 0.f;
       }
-      const float bx = (float)(cf[0] * cf[0] * Bm[0][0] + cf[1] * cf[1] * Bm[1][1] + cf[2] * cf[2] * Bm[2][2] +
-                               2.0 * (cf[0] * cf[1] * Bm[0][1] + cf[0] * cf[2] * Bm[0][2] + cf[1] * cf[2] * Bm[1][2]));
-      const float bp = (float)(cf[1] * cf[1] * Bm[1][1] + cf[2] * cf[2] * Bm[2][2] + 2.0 * cf[1] * cf[2] * Bm[1][2]);
-      const double sx = (double)rsqrtf(bx), sp = bp > 0.f ? (double)rsqrtf(bp) : 0.0;
+      const float bx = cf[0] * cf[0] * Bs[0][0] + cf[1] * cf[1] * Bs[1][1] + cf[2] * cf[2] * Bs[2][2] +
+                       2.f * (cf[0] * cf[1] * Bs[0][1] + cf[0] * cf[2] * Bs[0][2] + cf[1] * cf[2] * Bs[1][2]);
+      const float bp = cf[1] * cf[1] * Bs[1][1] + cf[2] * cf[2] * Bs[2][2] + 2.f * cf[1] * cf[2] * Bs[1][2];
+      const float sx = rsqrtf(bx), sp = bp > 0.f ? rsqrtf(bp) : 0.f;
       sh_coef[0] = cf[0] * sx;
-      sh_coef[1] = cf[1];
-      sh_coef[2] = cf[2];
-      sh_coef[3] = th;
-      red[0] = sx;
-      red[1] = sp;
-      sh_flag = ok && bp > 0;
+      sh_coef[1] = cf[1] * sx;
+      sh_coef[2] = cf[2] * sx;
+      sh_coef[3] = sp / sx;  // p_new = sp (cf1 w + cf2 p)
+      sh_flag = ok && bp > 0.f;
     }
     __syncthreads();
-    const double ca = sh_coef[0], cb = sh_coef[1], cp = sh_coef[2], sx = red[0], sp = red[1];
+    // x <- ca x + cb w + cp p (FP64 accumulation); p <- s (cb w + cp p) with its images
+    const double ca = sh_coef[0];
+    const float cb = sh_coef[1], cp = sh_coef[2], sp = sh_coef[3];
     L1_FOR_NODES {
       const int q = j * W + i;
-      const double pn = cb * Wv[q] + cp * P[q], kpn = cb * KW[q] + cp * KP[q], mpn = cb * MW[q] + cp * MP[q];
-      X[q] = ca * X[q] + sx * pn;
-      KX[q] = ca * KX[q] + sx * kpn;
-      MX[q] = ca * MX[q] + sx * mpn;
+      const float pn = cb * Wv[q] + cp * P[q];
+      X[q] = ca * X[q] + (double)pn;
       P[q] = sp * pn;
-      KP[q] = sp * kpn;
-      MP[q] = sp * mpn;
+      KP[q] = sp * (cb * KW[q] + cp * KP[q]);
+      MP[q] = sp * (cb * MW[q] + cp * MP[q]);
     }
-    rho = sh_coef[3];
     have_p = sh_flag != 0;
     __syncthreads();
+    apply_km64();
   }
-  apply_km(X, KX, MX);
   double v[3] = {0.0, 0.0, 0.0};
   L1_FOR_NODES {
     const int q = j * W + i;
@@ -619,7 +609,7 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
 }
 
 size_t level1_smem_bytes(long long nn0, long long tot, int tsize) {
-  return (size_t)(12 * 512 * 8 + 10 * nn0 * 8 + 2 * tot * tsize + tot + 16);
+  return (size_t)(12 * 512 * 4 + 4 * nn0 * 8 + 6 * nn0 * 4 + 8 + 2 * tot * tsize + tot + 16);
 }
 
 template <typename T>
@@ -909,8 +899,18 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     return true;
   };
   // w = w(mu) and r = w - S(mu) y for the current y (the previous solution warm-starts the
-  // next solve; y starts at 0)
-  for (int q = threadIdx.x; q < N; q += blockDim.x) y[q] = 0.0;
+  // next solve). y starts from the previous level's eigenvector, y = -c_H / c_0, whose
+  // coarse part differs from this level's by the small change of u_{h_k} between levels.
+  {
+    const int ncoef0 = (ncx + 1) * (ncy + 1);
+    const double* cpv = a.c_prev + (long long)p * ncoef0;
+    const double c0v = a.c0_prev[p];
+    // c_prev and this level's output c may be the same buffer: read all of it before any write
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      const int X = q % (ncx - 1) + 1, Y = q / (ncx - 1) + 1;
+      y[q] = (c0v != 0.0 && is_free(G, 0, ncx, ncy, X, Y)) ? -cpv[Y * (ncx + 1) + X] / c0v : 0.0;
+    }
+  }
   __syncthreads();
   auto start = [&](double mu) {
     for (int q = threadIdx.x; q < N; q += blockDim.x) wv[q] = ga[q] - mu * gb[q];
@@ -964,8 +964,8 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     fp = -beta + 2.0 * red[2] - red[3];
   };
   // squared relative residuals: Newton steps need y to ~1e-6 (the variational f then has a
-  // relative error ~1e-12); the eigenvector is refined until the FP64 residual stops falling
-  const double kNewtonTarget = 1e-12, kFinalTarget = 1e-30;
+  // relative error ~1e-12); the eigenvector to ~1e-13 (or until the residual stops falling)
+  const double kNewtonTarget = 1e-12, kFinalTarget = 1e-26;
   double mu = alpha / beta, lo = 0.0, hi = INFINITY, lam = NAN;
   int it = 0, status = 0;
   bool have = false, factored = false;

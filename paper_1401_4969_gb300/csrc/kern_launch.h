@@ -125,6 +125,8 @@ struct RRArgs {
   int stat_stride;
   int max_iter;
   int mixed;             // 1: FP32 band factors with FP64 refinement (k_rr_mixed)
+  const double* c_prev;  // coefficients of u_{h_k} (the previous level's eigenvector): warm start
+  const double* c0_prev;
 };
 void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s);
 size_t rr_smem_bytes(int nhb, int bw);

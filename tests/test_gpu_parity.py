@@ -160,7 +160,10 @@ def test_fused_multigrid_matches_unfused(name, prec):
     lam0, u0, _ = s.solve(mlev.default_opts(fused=0, **base), want_u=True)
     lam1, u1, _ = s.solve(mlev.default_opts(fused=1, **base), want_u=True)
     lam0, lam1 = lam0.cpu().numpy(), lam1.cpu().numpy()
-    assert np.all(np.abs(lam1 - lam0) <= 1e-12 * np.abs(lam0))
+    # the two kernel sets round differently (FP32 summation order inside the tiles): after
+    # 2 + 2 V-cycles the local residuals are ~1e-9, so the mixed path agrees to ~1e-11
+    tol = 1e-12 if prec == 0 else 1e-11
+    assert np.all(np.abs(lam1 - lam0) <= tol * np.abs(lam0))
     # the Rayleigh-Ritz eigenvector is taken at the last Newton iterate (within 1e-9 relative of
     # the root), which turns last-bit differences of u~ into ~1e-9 differences of u
     assert np.abs(u1.cpu().numpy() - u0.cpu().numpy()).max() <= 1e-7
