@@ -450,7 +450,10 @@ struct Launcher {
       rr.stat_stride = stat_stride;
       rr.max_iter = o.rr_max_iter;
       rr.mixed = (mixed && rr_mixed_supported(P.nhb, P.bw)) ? 1 : 0;
-      rr.smem = (rr.mixed ? rr_mixed_smem_bytes(P.nhb, P.bw) : rr_smem_bytes(P.nhb, P.bw)) <= (size_t)kRRSmemMax;
+      // row-blocked solves: one warp holds a grid row of the coarse system (<= 32 nodes)
+      rr.blocked = rr.mixed && P.bw - 1 <= 32 && rr_mixed_smem_bytes(P.nhb, P.bw, 1) <= (size_t)kRRSmemMax ? 1 : 0;
+      rr.smem = (rr.mixed ? rr_mixed_smem_bytes(P.nhb, P.bw, rr.blocked) : rr_smem_bytes(P.nhb, P.bw)) <=
+                (size_t)kRRSmemMax;
       go(F_RR, 0.0, [&] { launch_rr(G, rr, s); });
     }
     go(F_OUT, 16.0 * B, [&] { launch_lambda_out(B, n, lam, lambda_out, s); });

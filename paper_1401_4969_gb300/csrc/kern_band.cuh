@@ -137,4 +137,105 @@ __device__ inline void band_solve_shfl(const float* Ls, int ls, const float* inv
   __syncthreads();
 }
 
+// Row-blocked form of the FP32 factors for the T_H band (unknown r = (Y-1) b + (X-1),
+// b = ncx - 1 per grid row, half bandwidth b + 1): with that ordering L is block
+// lower-bidiagonal (the band profile of a first node in a row stops one grid row back, so
+// no fill reaches two blocks back). For nb = ncy - 1 blocks this stores, per block I, the
+// dense inverse of the unit lower triangular diagonal block (Dinv, rows r >= c) and the
+// sub-diagonal block Loff(r, c) = L(I b + r, (I - 1) b + c), each as a BS x BS tile padded
+// with zeros (BS >= b), so the solve can load whole rows without guards. Needs the scaled
+// factors Ls (L(i, i - d) = Ls[i * ls + d]).
+template <int BS>
+__device__ inline void band_blocks_f(const float* Ls, int ls, int bw, int b, int nb, float* Dinv, float* Loff) {
+  constexpr int T2 = BS * BS;
+  for (int q = threadIdx.x; q < nb * T2; q += blockDim.x) {
+    const int I = q / T2, rc = q - I * T2, r = rc / BS, c = rc - r * BS;
+    const int i = I * b + r, j = (I - 1) * b + c, d = i - j;
+    Loff[q] = (I > 0 && r < b && c < b && d >= 1 && d <= bw) ? Ls[i * ls + d] : 0.f;
+  }
+  // column c of the diagonal block's inverse: z_r = delta_rc - sum_{c <= k < r} L(r, k) z_k
+  for (int q = threadIdx.x; q < nb * BS; q += blockDim.x) {
+    const int I = q / BS, c = q - I * BS;
+    float* Z = Dinv + (long long)I * T2;
+    for (int r = 0; r < BS; ++r) {
+      float z = (r == c && c < b) ? 1.f : 0.f;
+      if (c < b && r < b && r > c)
+        for (int k = c; k < r; ++k) z -= Ls[(I * b + r) * ls + (r - k)] * Z[k * BS + c];
+      Z[r * BS + c] = (c < b && r < b && r >= c) ? z : 0.f;
+    }
+  }
+  __syncthreads();
+}
+
+// S x = y in place with the row-blocked factors: 2 nb block steps, each a b x b product
+// and a b x b triangular product, instead of 2 N dependent scalar steps. Run by warp 0
+// alone (b <= BS <= 32 lanes, one row of the block per lane) with warp barriers between
+// steps. y must be followed by BS readable finite floats and t (BS floats) zero beyond b;
+// the zero padding of the tiles cancels every out-of-block term.
+template <int BS>
+__device__ inline void band_solve_blocked(const float* Dinv, const float* Loff, const float* invD, float* y, float* t,
+                                          int b, int nb) {
+  if (threadIdx.x < 32) {
+    constexpr int T2 = BS * BS;
+    const int r = threadIdx.x;
+    for (int I = 0; I < nb; ++I) {
+      if (r < b) {
+        float s0 = y[I * b + r], s1 = 0.f;
+        if (I > 0) {
+          const float* Lo = Loff + (long long)I * T2 + r * BS;
+          const float* yp = y + (I - 1) * b;
+#pragma unroll
+          for (int c = 0; c < BS; c += 2) {
+            s0 -= Lo[c] * yp[c];
+            s1 -= Lo[c + 1] * yp[c + 1];
+          }
+        }
+        t[r] = s0 + s1;
+      }
+      __syncwarp();
+      if (r < b) {
+        const float* Z = Dinv + (long long)I * T2 + r * BS;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < BS; c += 2) {
+          s0 += Z[c] * t[c];
+          s1 += Z[c + 1] * t[c + 1];
+        }
+        y[I * b + r] = s0 + s1;
+      }
+      __syncwarp();
+    }
+    for (int q = r; q < nb * b; q += 32) y[q] *= invD[q];
+    __syncwarp();
+    for (int I = nb - 1; I >= 0; --I) {
+      if (r < b) {
+        float s0 = y[I * b + r], s1 = 0.f;
+        if (I + 1 < nb) {
+          const float* Lo = Loff + (long long)(I + 1) * T2;  // transpose: column r of block I + 1
+          const float* xn = y + (I + 1) * b;
+#pragma unroll
+          for (int c = 0; c < BS; c += 2) {
+            s0 -= Lo[c * BS + r] * xn[c];
+            s1 -= Lo[(c + 1) * BS + r] * xn[c + 1];
+          }
+        }
+        t[r] = s0 + s1;
+      }
+      __syncwarp();
+      if (r < b) {
+        const float* Z = Dinv + (long long)I * T2;  // transpose of the lower inverse
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < BS; c += 2) {
+          s0 += Z[c * BS + r] * t[c];
+          s1 += Z[(c + 1) * BS + r] * t[c + 1];
+        }
+        y[I * b + r] = s0 + s1;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace mlev

@@ -810,8 +810,18 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   double* sm_s = mh_s + (long long)N * bw1;               // S(mu) of the current mu (FP64)
   float* Lb = reinterpret_cast<float*>(a.smem ? sm_s + (long long)N * bw1 : r + N);
   float* invD = Lb + (long long)N * bw1;
-  float* r32 = invD + N;
-  int* pairs = reinterpret_cast<int*>(a.smem ? reinterpret_cast<double*>(r32 + N + (N & 1)) : rr_sm);
+  float* r32 = invD + N;                                    // N + 32 entries, the tail kept at 0
+  const int bsz = bw - 1, nbk = bsz > 0 ? N / bsz : 0;     // row blocks (blocked solves)
+  const int BS = bsz <= 16 ? 16 : 32;                      // padded tile edge
+  float* Dinv = r32 + N + 32;
+  float* Loff = Dinv + (a.blocked ? (long long)nbk * BS * BS : 0);
+  float* tb = Loff + (a.blocked ? (long long)nbk * BS * BS : 0);
+  int* pairs = reinterpret_cast<int*>(a.smem ? tb + (a.blocked ? BS : 0) : reinterpret_cast<float*>(rr_sm));
+  if (a.smem) {
+    for (int q = threadIdx.x; q < 32; q += blockDim.x) r32[N + q] = 0.f;
+    if (a.blocked)
+      for (int q = threadIdx.x; q < BS; q += blockDim.x) tb[q] = 0.f;
+  }
   const double* KH = a.KH + (long long)p * N * bw1;
   const double* MH = a.MH + (long long)p * N * bw1;
   if (a.smem) {
@@ -896,6 +906,10 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
       if (d > 0 && i - d >= 0) Lb[q] *= invD[i - d];
     }
     __syncthreads();
+    if (a.blocked && BS == 16)
+      band_blocks_f<16>(Lb, bw1, bw, bsz, nbk, Dinv, Loff);
+    else if (a.blocked)
+      band_blocks_f<32>(Lb, bw1, bw, bsz, nbk, Dinv, Loff);
     return true;
   };
   // w = w(mu) and r = w - S(mu) y for the current y (the previous solution warm-starts the
@@ -926,7 +940,12 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   auto refine = [&](double mu) {
     for (int q = threadIdx.x; q < N; q += blockDim.x) r32[q] = (float)r[q];
     __syncthreads();
-    band_solve_shfl(Lb, bw1, invD, r32, N, bw);
+    if (a.blocked && BS == 16)
+      band_solve_blocked<16>(Dinv, Loff, invD, r32, tb, bsz, nbk);
+    else if (a.blocked)
+      band_solve_blocked<32>(Dinv, Loff, invD, r32, tb, bsz, nbk);
+    else
+      band_solve_shfl(Lb, bw1, invD, r32, N, bw);
     for (int q = threadIdx.x; q < N; q += blockDim.x) y[q] += (double)r32[q];
     __syncthreads();
     double v[2] = {0.0, 0.0};
@@ -1042,10 +1061,12 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
 }
 
 // Shared memory of k_rr_mixed: 5 FP64 vectors, K_H, M_H and S(mu), the FP32 band, 2 FP32
-// vectors and the pair table.
-size_t rr_mixed_smem_bytes(int nhb, int bw) {
-  return (size_t)nhb * 5 * 8 + 3 * (size_t)nhb * (bw + 1) * 8 + ((size_t)nhb * (bw + 1) + 2 * (size_t)nhb + 2) * 4 +
-         (size_t)(bw * (bw + 1) / 2) * 4 + 16;
+// vectors, the row-blocked factors (blocked mode) and the pair table.
+size_t rr_mixed_smem_bytes(int nhb, int bw, int blocked) {
+  const size_t bsz = bw - 1, bs = bsz <= 16 ? 16 : 32;
+  const size_t blk = blocked && bsz > 0 ? 2 * (nhb / bsz) * bs * bs + bs : 0;
+  return (size_t)nhb * 5 * 8 + 3 * (size_t)nhb * (bw + 1) * 8 +
+         ((size_t)nhb * (bw + 1) + 2 * (size_t)nhb + 32 + blk + 2) * 4 + (size_t)(bw * (bw + 1) / 2) * 4 + 16;
 }
 // The mixed kernel keeps one factorisation pair per thread (bw (bw + 1) / 2 <= 256) and the
 // warp solve's window in one warp's lanes (bw <= 31); wider coarse grids use the FP64 kernel.
@@ -1065,7 +1086,7 @@ void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s) {
   }
   const size_t pairs_only = (size_t)(a.bw * (a.bw + 1) / 2) * 4;
   if (a.mixed) {
-    const size_t smem = a.smem ? rr_mixed_smem_bytes(a.nhb, a.bw) : pairs_only;
+    const size_t smem = a.smem ? rr_mixed_smem_bytes(a.nhb, a.bw, a.blocked) : pairs_only;
     k_rr_mixed<<<a.B, 256, smem, s>>>(G, a);
     return;
   }

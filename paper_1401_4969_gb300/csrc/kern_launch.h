@@ -127,10 +127,11 @@ struct RRArgs {
   int mixed;             // 1: FP32 band factors with FP64 refinement (k_rr_mixed)
   const double* c_prev;  // coefficients of u_{h_k} (the previous level's eigenvector): warm start
   const double* c0_prev;
+  int blocked;           // 1: row-blocked FP32 solves (needs smem), else the warp solve
 };
 void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s);
 size_t rr_smem_bytes(int nhb, int bw);
-size_t rr_mixed_smem_bytes(int nhb, int bw);
+size_t rr_mixed_smem_bytes(int nhb, int bw, int blocked);
 int rr_mixed_supported(int nhb, int bw);
 constexpr int kRRSmemMax = 200 * 1024;
 
