@@ -75,7 +75,9 @@ typedef struct mlev_opts {
   int check_residuals;  /* 1: measure the final relative residual of every local / G_{m+1} solve */
   int profile;          /* 1: time every launch with CUDA events (no graph); read with mlev_profile_read */
   int fused;            /* 1: fused multigrid kernels (down / up / shared-memory tail); 0: one launch per operation */
-  int reserved[3];
+  int tail_nodes;       /* largest grid (nodes) the in-block tail of a fused V-cycle takes on; 0 = as many
+                           levels as fit in shared memory */
+  int reserved[2];
 } mlev_opts;
 
 /* Per-solve diagnostics (batch member 0 unless noted). */

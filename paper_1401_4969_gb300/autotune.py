@@ -10,7 +10,8 @@ coefficient). The tuner measures it on the device:
    member's eigenvalue is within `safety * target_rel` of the reference,
 3. a staged search: first the cycle counts (vcycles, refine_passes, strip_vcycles) in
    increasing order of work, then the smoothing sweeps and coarsest-grid sweeps of the
-   cheapest accepted schedule, then the fused / unfused multigrid kernels.
+   cheapest accepted schedule, then the size of the one-block tail of the fused V-cycle
+   and the fused / unfused multigrid kernels.
 
 The fastest accepted schedule is cached in a JSON file keyed by the problem's signature,
 the precision, the target and the device name.
@@ -24,7 +25,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-TUNE_KEYS = ("vcycles", "refine_passes", "strip_vcycles", "pre_smooth", "post_smooth", "coarse_sweeps", "fused")
+TUNE_KEYS = ("vcycles", "refine_passes", "strip_vcycles", "pre_smooth", "post_smooth", "coarse_sweeps", "fused",
+             "tail_nodes")
 
 
 def default_cache_path() -> str:
@@ -90,7 +92,7 @@ def search(evaluate, target_rel: float, safety: float = 0.1, base: dict | None =
     Stage 1 walks the cycle candidates in increasing work and stops after `max_accept`
     accepted schedules; stage 2 lowers the smoothing and coarsest sweeps of the fastest
     accepted one; stage 3 compares the fused and unfused multigrid kernels."""
-    base = dict(base or {"pre_smooth": 2, "post_smooth": 2, "coarse_sweeps": 40, "fused": 1})
+    base = dict(base or {"pre_smooth": 2, "post_smooth": 2, "coarse_sweeps": 40, "fused": 1, "tail_nodes": 0})
     tol = safety * target_rel
     trials: list[Trial] = []
 
@@ -116,6 +118,11 @@ def search(evaluate, target_rel: float, safety: float = 0.1, base: dict | None =
             t = run({**best.opts, key: v})
             if t.ok and t.ms < best.ms:
                 best = t
+    # tile choice: how large a grid the one-block tail of the fused V-cycle takes on
+    for tn in (4096, 1024):
+        t = run({**best.opts, "fused": 1, "tail_nodes": tn})
+        if t.ok and t.ms < best.ms:
+            best = t
     t = run({**best.opts, "fused": 1 - best.opts.get("fused", 1)})
     if t.ok and t.ms < best.ms:
         best = t

@@ -40,6 +40,8 @@ struct mlev_ctx {
   // plan cache: the planner runs again only when the setup or the precision changes
   long long built_version = -1;
   int built_precision = -1;
+  int built_tail_nodes = -1;
+  long long plan_gen = 0;  // bumped on every plan rebuild (keys the table upload)
   // profiling
   std::vector<cudaEvent_t> ev_pool;
   std::vector<ProfRecHost> prof;
@@ -75,14 +77,14 @@ bool opts_valid(const mlev_opts* o) {
   return o && (o->precision == MLEV_PREC_FP64 || o->precision == MLEV_PREC_MIXED) && o->vcycles >= 1 &&
          o->refine_passes >= 1 && o->strip_vcycles >= 1 && o->pre_smooth >= 0 && o->post_smooth >= 0 &&
          o->pre_smooth + o->post_smooth >= 1 && o->coarse_sweeps >= 1 && o->level1_max_iter >= 1 &&
-         o->level1_tol > 0 && o->rr_max_iter >= 1 && o->omega > 0 && o->omega < 2;
+         o->level1_tol > 0 && o->rr_max_iter >= 1 && o->omega > 0 && o->omega < 2 && o->tail_nodes >= 0;
 }
 
 std::string opts_key(const mlev_opts* o) {
   char b[256];
-  snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%.17g/%d/%.17g/%d/%d", o->precision, o->vcycles,
+  snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%.17g/%d/%.17g/%d/%d/%d", o->precision, o->vcycles,
            o->refine_passes, o->strip_vcycles, o->pre_smooth, o->post_smooth, o->coarse_sweeps, o->level1_max_iter,
-           o->level1_tol, o->rr_max_iter, o->omega, o->check_residuals, o->fused);
+           o->level1_tol, o->rr_max_iter, o->omega, o->check_residuals, o->fused, o->tail_nodes);
   return b;
 }
 
@@ -640,11 +642,15 @@ struct Launcher {
 };
 
 int ensure_plan(mlev_ctx* ctx, const mlev_opts* o) {
-  if (ctx->built_version == ctx->version && ctx->built_precision == o->precision) return MLEV_OK;
+  if (ctx->built_version == ctx->version && ctx->built_precision == o->precision &&
+      ctx->built_tail_nodes == o->tail_nodes)
+    return MLEV_OK;
   int rc = map_plan_error(ctx, ctx->plan.build(*o));
   if (rc) return rc;
   ctx->built_version = ctx->version;
   ctx->built_precision = o->precision;
+  ctx->built_tail_nodes = o->tail_nodes;
+  ctx->plan_gen++;
   return MLEV_OK;
 }
 
@@ -710,7 +716,7 @@ std::string encode_tensor_maps(const Plan& P, void* ws, char* host) {
 
 int upload_tables(mlev_ctx* ctx, void* ws, cudaStream_t s, bool force) {
   Plan& P = ctx->plan;
-  const long long key = ctx->version * 2 + ctx->built_precision;
+  const long long key = ctx->plan_gen;
   if (!force && ctx->uploaded_ws == ws && ctx->uploaded_version == key) return MLEV_OK;
   std::vector<char> host(P.tables_bytes, 0);
   auto put = [&](const Span& sp, const void* src, size_t bytes) {

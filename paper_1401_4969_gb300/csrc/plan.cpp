@@ -135,6 +135,7 @@ static bool block_has_unknown(const Plan& p, const GridDesc& g, int x0, int y0, 
 std::string Plan::build(const mlev_opts& o) {
   if (!ready()) return "STATE: set domain, partition, levels and forms before solving";
   tsize = o.precision == MLEV_PREC_FP64 ? 8 : 4;
+  tail_nodes = o.tail_nodes;
   std::string err = check_partition(*this);
   if (!err.empty()) return err;
 
@@ -391,8 +392,14 @@ std::string Plan::build(const mlev_opts& o) {
       tail_smem = 0;
       for (int d = 0; d <= D; ++d) {
         size_t need = 0;
-        for (int gi : by_depth[d]) need = std::max(need, tail_bytes(gi, D - d + 1, extra));
-        if (need <= kTailBudget) {
+        long long nodes = 0;
+        for (int gi : by_depth[d]) {
+          need = std::max(need, tail_bytes(gi, D - d + 1, extra));
+          nodes = std::max(nodes, (long long)(grids[gi].nx + 1) * (grids[gi].ny + 1));
+        }
+        // the tail is one block per job: cap its first grid so the larger grids keep the
+        // tiled (many-block) kernels; the coarsest grid always goes to the tail
+        if (need <= kTailBudget && (tail_nodes <= 0 || nodes <= tail_nodes || d == D)) {
           dt = d;
           tail_smem = need;
           break;
