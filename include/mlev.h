@@ -74,7 +74,9 @@ typedef struct mlev_opts {
   double omega;         /* over-relaxation of the red-black Gauss-Seidel smoother (1 = plain GS) */
   int check_residuals;  /* 1: measure the final relative residual of every local / G_{m+1} solve */
   int profile;          /* 1: time every launch with CUDA events (no graph); read with mlev_profile_read */
-  int fused;            /* 1: fused multigrid kernels (down / up / shared-memory tail); 0: one launch per operation */
+  int fused;            /* 1: fused multigrid kernels (down / up / shared-memory tail); 0: one launch per
+                           operation; 2: one launch per operation on the large grids, the shared-memory
+                           tail for the small ones (see tail_nodes) */
   int tail_nodes;       /* largest grid (nodes) the in-block tail of a fused V-cycle takes on; 0 = as many
                            levels as fit in shared memory */
   int reserved[2];

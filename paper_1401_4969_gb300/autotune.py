@@ -118,14 +118,12 @@ def search(evaluate, target_rel: float, safety: float = 0.1, base: dict | None =
             t = run({**best.opts, key: v})
             if t.ok and t.ms < best.ms:
                 best = t
-    # tile choice: how large a grid the one-block tail of the fused V-cycle takes on
-    for tn in (4096, 1024):
-        t = run({**best.opts, "fused": 1, "tail_nodes": tn})
+    # kernel choice: fused tiles, one launch per operation, or the hybrid (per-operation
+    # kernels on large grids, the one-block tail below tail_nodes), and the tail's size
+    for fused, tn in ((0, 0), (2, 4096), (2, 1024), (2, 256), (1, 4096), (1, 1024)):
+        t = run({**best.opts, "fused": fused, "tail_nodes": tn})
         if t.ok and t.ms < best.ms:
             best = t
-    t = run({**best.opts, "fused": 1 - best.opts.get("fused", 1)})
-    if t.ok and t.ms < best.ms:
-        best = t
     return TuneResult(opts={k: best.opts[k] for k in TUNE_KEYS if k in best.opts}, ms=best.ms, err=best.err,
                       target_rel=target_rel, trials=trials)
 

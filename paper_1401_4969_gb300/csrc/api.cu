@@ -77,7 +77,8 @@ bool opts_valid(const mlev_opts* o) {
   return o && (o->precision == MLEV_PREC_FP64 || o->precision == MLEV_PREC_MIXED) && o->vcycles >= 1 &&
          o->refine_passes >= 1 && o->strip_vcycles >= 1 && o->pre_smooth >= 0 && o->post_smooth >= 0 &&
          o->pre_smooth + o->post_smooth >= 1 && o->coarse_sweeps >= 1 && o->level1_max_iter >= 1 &&
-         o->level1_tol > 0 && o->rr_max_iter >= 1 && o->omega > 0 && o->omega < 2 && o->tail_nodes >= 0;
+         o->level1_tol > 0 && o->rr_max_iter >= 1 && o->omega > 0 && o->omega < 2 && o->tail_nodes >= 0 &&
+         o->fused >= 0 && o->fused <= 2;
 }
 
 std::string opts_key(const mlev_opts* o) {
@@ -237,14 +238,54 @@ struct Launcher {
          [&] { launch_mg_up<T>(G, tiles_at(fl[d]), fl[d].count, X, F, o.post_smooth, o.omega, s); });
   }
 
+  // Hybrid V-cycle (opts.fused = 2): one launch per operation on the depths above the tail
+  // (large grids, many blocks), then the tail kernel for every coarser grid of the jobs.
+  template <typename T>
+  void vcycle_hybrid(const std::vector<TileList>& lists, int dt, int D, const TileList& tail, size_t tail_smem, T* X,
+                     T* F, bool direct) {
+    const double t = sizeof(T);
+    auto smooth = [&](int d, int color) {
+      go(F_SMOOTH, (2 * t + 0.5 * kfine_extra()) * lists[d].unk,
+         [&] { launch_smooth<T>(G, tiles_at(lists[d]), lists[d].count, X, F, color, o.omega, s); });
+    };
+    for (int d = 0; d < dt; ++d) {
+      for (int k = 0; k < o.pre_smooth; ++k) {
+        smooth(d, 0);
+        smooth(d, 1);
+      }
+      go(F_RESTRICT, (10 * t + 4 * kfine_extra()) * lists[d + 1].unk,
+         [&] { launch_restrict<T>(G, tiles_at(lists[d + 1]), lists[d + 1].count, X, F, s); });
+    }
+    const T* inv = direct ? at<T>(ws, P.w_cinv) : nullptr;
+    if (dt == D && !direct && coarsest_smem_bytes(P.kappa_kind, P.strip_coarse_nodes, sizeof(T)) <= 220 * 1024) {
+      go(F_COARSEST, 4 * t * tail.unk, [&] {
+        launch_coarsest_smem<T>(G, tiles_at(tail), tail.count, P.strip_coarse_nodes, X, F, o.coarse_sweeps, o.omega,
+                                s);
+      });
+    } else {
+      go(F_MG_TAIL, 3.0 * t * tail.unk, [&] {
+        launch_mg_tail<T>(G, tiles_at(tail), tail.count, X, F, inv, direct ? P.nd_max : 0, D - dt + 1, o.pre_smooth,
+                          o.post_smooth, o.coarse_sweeps, o.omega, dt == 0 ? 1 : 0, tail_smem, s);
+      });
+    }
+    for (int d = dt - 1; d >= 0; --d) {
+      go(F_PROLONG, 2.25 * t * lists[d].unk, [&] { launch_prolong<T>(G, tiles_at(lists[d]), lists[d].count, X, s); });
+      for (int k = 0; k < o.post_smooth; ++k) {
+        smooth(d, 1);
+        smooth(d, 0);
+      }
+    }
+  }
+
   // passes of V-cycles with FP64 residual refinement in between (mixed) on one job set
   template <typename T>
   void solve_set(const std::vector<TileList>& lists, const TileList& coarsest, int vcycles, T* X, T* F, double* X64,
                  const double* R, int cmode, const std::vector<TileList>* fl = nullptr, int dt = 0,
                  const TileList* tail = nullptr, size_t tail_smem = 0, bool rmask = false) {
     const int D = (int)lists.size() - 1;
-    const bool fused = o.fused && fl && tail && dt <= D && o.pre_smooth >= 1 && o.pre_smooth <= 2 &&
+    const bool fused = o.fused == 1 && fl && tail && dt <= D && o.pre_smooth >= 1 && o.pre_smooth <= 2 &&
                        o.post_smooth >= 1 && o.post_smooth <= 2;
+    const bool hybrid = o.fused == 2 && tail && dt <= D;
     const bool mixed = sizeof(T) == 4;
     const double t = sizeof(T);
     const int passes = mixed ? o.refine_passes : 1;
@@ -263,6 +304,8 @@ struct Launcher {
       for (int v = 0; v < cyc; ++v) {
         if (fused)
           vcycle_fused<T>(*fl, dt, D, *tail, tail_smem, X, F, cmode == C_DIRECT);
+        else if (hybrid)
+          vcycle_hybrid<T>(lists, dt, D, *tail, tail_smem, X, F, cmode == C_DIRECT);
         else
           vcycle<T>(lists, coarsest, X, F, cmode);
       }
