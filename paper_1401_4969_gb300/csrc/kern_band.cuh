@@ -238,4 +238,163 @@ __device__ inline void band_solve_blocked(const float* Dinv, const float* Loff, 
   __syncthreads();
 }
 
+// Block LDL^T of the T_H pencil S = K_H - mu M_H by grid rows (FP32), for unknowns ordered
+// r = (Y-1) b + (X-1): S is block tridiagonal with b x b diagonal blocks S_II (couplings
+// W/E) and sub-diagonal blocks S_{I,I-1} holding only the S and SW couplings (row r: columns
+// r and r - 1). With W_I = S_{I,I-1} P_{I-1}^{-1} and P_I = S_II - W_I S_{I,I-1}^T
+// (P_0 = S_00), S = L P L^T with L unit block lower bidiagonal (L_{I,I-1} = W_I) and P block
+// diagonal; the blocks are stored as BS x BS tiles (zero padded): Pinv[I] = P_I^{-1} and
+// W[I]. Sparse S_{I,I-1} makes W_I and P_I O(b^2) each; P_I is inverted by warp 0 alone
+// (Gauss-Jordan, row per lane, warp barriers). The band S(mu) (FP64, [r][d] = S(r, r-d))
+// is read from shared memory. `work` holds 2 BS x BS tiles. Returns false (to all threads)
+// if a pivot is not positive (S(mu) not positive definite); `flag` is a shared int.
+template <int BS>
+__device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pinv, float* W, float* work, int* flag) {
+  constexpr int T2 = BS * BS;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  float* A = work;        // P_I, inverted in place
+  float* Sub = work + T2; // dense copy of S_{I,I-1} (rows r: cols r, r-1)
+  auto s_at = [&](int i, int j) -> float {  // S(i, j) for |i - j| <= bw from the band
+    return i >= j ? (float)Sb[(long long)i * bw1 + (i - j)] : (float)Sb[(long long)j * bw1 + (j - i)];
+  };
+  if (tid == 0) *flag = 1;
+  for (int I = 0; I < nb; ++I) {
+    const float* Pp = Pinv + (long long)(I - 1) * T2;
+    float* Wi = W + (long long)I * T2;
+    // S_{I,I-1} (two nonzeros per row) and W_I = S_{I,I-1} P_{I-1}^{-1}
+    if (I > 0) {
+      for (int q = tid; q < T2; q += nt) {
+        const int r = q / BS, c = q % BS;
+        float v = 0.f;
+        if (r < b && c < b) {
+          const int i = I * b + r, j = (I - 1) * b + c;
+          if (c == r || c == r - 1) v = s_at(i, j);
+        }
+        Sub[q] = v;
+      }
+      __syncthreads();
+      for (int q = tid; q < T2; q += nt) {
+        const int r = q / BS, c = q % BS;
+        float v = Sub[r * BS + r] * Pp[r * BS + c];
+        if (r > 0) v += Sub[r * BS + r - 1] * Pp[(r - 1) * BS + c];
+        Wi[q] = (r < b && c < b) ? v : 0.f;
+      }
+      __syncthreads();
+    } else {
+      for (int q = tid; q < T2; q += nt) Wi[q] = 0.f;
+    }
+    // P_I = S_II - W_I S_{I,I-1}^T  ((S^T)_{kc} nonzero for k = c, c - 1... i.e. Sub[c][k], k in {c, c-1})
+    for (int q = tid; q < T2; q += nt) {
+      const int r = q / BS, c = q % BS;
+      float v = 0.f;
+      if (r < b && c < b) {
+        const int i = I * b + r, j = I * b + c;
+        if (r - c <= 1 && c - r <= 1) v = s_at(i, j);
+        if (I > 0) {
+          v -= Wi[r * BS + c] * Sub[c * BS + c];
+          if (c > 0) v -= Wi[r * BS + c - 1] * Sub[c * BS + c - 1];
+        }
+      } else if (r == c) {
+        v = 1.f;  // padding: identity keeps the inverse's padding at zero off the diagonal
+      }
+      A[q] = v;
+    }
+    __syncthreads();
+    // Gauss-Jordan on A (symmetric positive definite): warp 0, lane = row
+    if (tid < 32) {
+      float* Pi = Pinv + (long long)I * T2;
+      const int r = tid;
+      float row[BS], inv_row[BS];
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        row[c] = r < BS ? A[r * BS + c] : 0.f;
+        inv_row[c] = (r == c) ? 1.f : 0.f;
+      }
+      int ok = 1;
+#pragma unroll
+      for (int k = 0; k < BS; ++k) {
+        const float pv = __shfl_sync(0xffffffffu, row[k], k);
+        if (!(pv > 0.f)) ok = 0;
+        const float ip = 1.0f / pv;
+        float prow[BS], pinv[BS];
+#pragma unroll
+        for (int c = 0; c < BS; ++c) {
+          prow[c] = __shfl_sync(0xffffffffu, row[c], k) * ip;
+          pinv[c] = __shfl_sync(0xffffffffu, inv_row[c], k) * ip;
+        }
+        const float f = row[k];
+#pragma unroll
+        for (int c = 0; c < BS; ++c) {
+          if (r == k) {
+            row[c] = prow[c];
+            inv_row[c] = pinv[c];
+          } else {
+            row[c] -= f * prow[c];
+            inv_row[c] -= f * pinv[c];
+          }
+        }
+      }
+      if (r < BS)
+#pragma unroll
+        for (int c = 0; c < BS; ++c) Pi[r * BS + c] = (r < b && c < b) ? inv_row[c] : 0.f;
+      if (r == 0 && !ok) *flag = 0;
+    }
+    __syncthreads();
+    if (!*flag) return false;
+  }
+  return true;
+}
+
+// S x = y in place with the block factors (L_{I,I-1} = W_I, P_I^{-1}): forward
+// u_I = y_I - W_I u_{I-1} (in place), backward x_I = P_I^{-1} u_I - W_{I+1}^T x_{I+1}, by
+// warp 0 (lane = row). y must be followed by BS readable finite floats; t is BS floats of
+// scratch.
+template <int BS>
+__device__ inline void block_solve_f(const float* Pinv, const float* W, float* y, float* t, int b, int nb) {
+  if (threadIdx.x < 32) {
+    constexpr int T2 = BS * BS;
+    const int r = threadIdx.x;
+    for (int I = 1; I < nb; ++I) {
+      if (r < b) {
+        const float* Wr = W + (long long)I * T2 + r * BS;
+        const float* up = y + (I - 1) * b;
+        float s0 = y[I * b + r], s1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < BS; c += 2) {
+          s0 -= Wr[c] * up[c];
+          s1 -= Wr[c + 1] * up[c + 1];
+        }
+        y[I * b + r] = s0 + s1;  // lane r alone reads and writes entry r of block I
+      }
+      __syncwarp();
+    }
+    for (int I = nb - 1; I >= 0; --I) {
+      if (r < b) {
+        const float* Pr = Pinv + (long long)I * T2 + r * BS;
+        const float* u = y + I * b;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < BS; c += 2) {
+          s0 += Pr[c] * u[c];
+          s1 += Pr[c + 1] * u[c + 1];
+        }
+        if (I + 1 < nb) {
+          const float* Wn = W + (long long)(I + 1) * T2;  // column r of W_{I+1}
+          const float* xn = y + (I + 1) * b;
+#pragma unroll
+          for (int c = 0; c < BS; c += 2) {
+            s0 -= Wn[c * BS + r] * xn[c];
+            s1 -= Wn[(c + 1) * BS + r] * xn[c + 1];
+          }
+        }
+        t[r] = s0 + s1;
+      }
+      __syncwarp();
+      if (r < b) y[I * b + r] = t[r];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace mlev

@@ -796,6 +796,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   extern __shared__ double rr_sm[];
   __shared__ double scratch[8 * 4];
   __shared__ double red[4];
+  __shared__ int bflag;
   const int p = blockIdx.x, N = a.nhb, bw = a.bw, bw1 = bw + 1;
   const int ncx = G.ncx, ncy = G.ncy;
   const int npair = bw * (bw + 1) / 2;
@@ -816,7 +817,8 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   float* Dinv = r32 + N + 32;
   float* Loff = Dinv + (a.blocked ? (long long)nbk * BS * BS : 0);
   float* tb = Loff + (a.blocked ? (long long)nbk * BS * BS : 0);
-  int* pairs = reinterpret_cast<int*>(a.smem ? tb + (a.blocked ? BS : 0) : reinterpret_cast<float*>(rr_sm));
+  float* bwork = tb + (a.blocked ? BS : 0);                // 2 BS x BS tiles (block factorisation)
+  int* pairs = reinterpret_cast<int*>(a.smem ? bwork + (a.blocked ? 2 * BS * BS : 0) : reinterpret_cast<float*>(rr_sm));
   if (a.smem) {
     for (int q = threadIdx.x; q < 32; q += blockDim.x) r32[N + q] = 0.f;
     if (a.blocked)
@@ -896,9 +898,20 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     return s;
   };
   double sig = NAN;  // shift of the current factors
-  // FP32 factors of S(mu), off-diagonals scaled to L; false if S(mu) is not positive definite
+  // FP32 factors of S(mu); false if S(mu) is not positive definite. Blocked mode: the block
+  // LDL^T by grid rows (P_I^{-1} in Dinv, W_I in Loff) from the staged FP64 band S(mu);
+  // otherwise the column band LDL^T with off-diagonals scaled to L.
   auto factor = [&](double mu) {
     sig = mu;
+    if (a.blocked) {
+      if (smu != mu) {
+        for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) sm_s[q] = kh_s[q] - mu * mh_s[q];
+        smu = mu;
+      }
+      __syncthreads();
+      return BS == 16 ? block_ldlt_f<16>(sm_s, bw1, bsz, nbk, Dinv, Loff, bwork, &bflag)
+                      : block_ldlt_f<32>(sm_s, bw1, bsz, nbk, Dinv, Loff, bwork, &bflag);
+    }
     for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) Lb[q] = (float)(KH[q] - mu * MH[q]);
     if (!band_ldlt_f(Lb, invD, pairs, npair, N, bw)) return false;
     for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) {
@@ -906,10 +919,6 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
       if (d > 0 && i - d >= 0) Lb[q] *= invD[i - d];
     }
     __syncthreads();
-    if (a.blocked && BS == 16)
-      band_blocks_f<16>(Lb, bw1, bw, bsz, nbk, Dinv, Loff);
-    else if (a.blocked)
-      band_blocks_f<32>(Lb, bw1, bw, bsz, nbk, Dinv, Loff);
     return true;
   };
   // w = w(mu) and r = w - S(mu) y for the current y (the previous solution warm-starts the
@@ -941,9 +950,9 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     for (int q = threadIdx.x; q < N; q += blockDim.x) r32[q] = (float)r[q];
     __syncthreads();
     if (a.blocked && BS == 16)
-      band_solve_blocked<16>(Dinv, Loff, invD, r32, tb, bsz, nbk);
+      block_solve_f<16>(Dinv, Loff, r32, tb, bsz, nbk);
     else if (a.blocked)
-      band_solve_blocked<32>(Dinv, Loff, invD, r32, tb, bsz, nbk);
+      block_solve_f<32>(Dinv, Loff, r32, tb, bsz, nbk);
     else
       band_solve_shfl(Lb, bw1, invD, r32, N, bw);
     for (int q = threadIdx.x; q < N; q += blockDim.x) y[q] += (double)r32[q];
@@ -1064,7 +1073,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
 // vectors, the row-blocked factors (blocked mode) and the pair table.
 size_t rr_mixed_smem_bytes(int nhb, int bw, int blocked) {
   const size_t bsz = bw - 1, bs = bsz <= 16 ? 16 : 32;
-  const size_t blk = blocked && bsz > 0 ? 2 * (nhb / bsz) * bs * bs + bs : 0;
+  const size_t blk = blocked && bsz > 0 ? 2 * (nhb / bsz) * bs * bs + bs + 2 * bs * bs : 0;
   return (size_t)nhb * 5 * 8 + 3 * (size_t)nhb * (bw + 1) * 8 +
          ((size_t)nhb * (bw + 1) + 2 * (size_t)nhb + 32 + blk + 2) * 4 + (size_t)(bw * (bw + 1) / 2) * 4 + 16;
 }
