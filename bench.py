@@ -189,6 +189,35 @@ def reference_arm(args):
     return 0
 
 
+def time_adjoint(mlev, W, torch, reps=5):
+    """dlambda/dkappa on the 512 x 512 per-triangle-kappa workload: forward solve time and
+    mlev_grad_kappa time (forward with level checkpoints + reverse sweep), default mixed opts."""
+    p = W.config5()
+    s = mlev.Solver(p)
+    o = mlev.default_opts(precision=mlev.PREC_MIXED)
+    lam, _ = s.alloc_outputs()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    fwd = timed(lambda: s.solve_into(o, lam))
+    grad = timed(lambda: s.grad_kappa(o))
+    s.close()
+    return {"workload": "c5: unit square 16x16, 4x4 subdomains, 5 levels (512x512), kappa per finest triangle",
+            "opts": "library defaults (mixed)", "forward_ms": fwd, "grad_ms": grad, "grad_over_forward": grad / fwd,
+            "dofs": 511 * 511}
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -200,6 +229,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel profiled pass")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing (512x512 kappa workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -321,6 +351,7 @@ def main():
             dist.destroy_process_group()
         return 0
 
+    adjoint = None if args.no_adjoint else time_adjoint(mlev, W, torch)
     peak, peak_kind = measured_peaks()
     dom = max(prof, key=lambda r: r["ms"])
     with_bytes = [r for r in prof if r["bytes"] > 0]
@@ -366,6 +397,7 @@ def main():
         "roofline": roofline,
         "profile": [{k: r[k] for k in ("name", "launches", "ms", "bytes")} for r in prof if r["launches"]],
         "clocks": clocks,
+        "adjoint": adjoint,
     }
     if cpu_base is not None:
         out, err = cpu_base.communicate()

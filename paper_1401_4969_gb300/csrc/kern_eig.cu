@@ -754,6 +754,19 @@ __global__ void __launch_bounds__(256) k_rr(DevGeom G, RRArgs a) {
   if (it >= a.max_iter) status |= MLEV_ST_RR_NOCONV;
   if (!(lam == lam)) lam = mu;
   if (!have && !factor_solve(mu)) status |= MLEV_ST_RR_BREAKDOWN;
+  // y at lambda rather than at the last iterate mu (where Newton stops varies with the
+  // input, and y(mu) differs from y(lambda) by O(lambda - mu) <= 1e-9): one correction step
+  // y <- S(mu)^{-1} [w(lambda) + (lambda - mu) M y(mu)] with the factors of S(mu), error
+  // O((lambda - mu)^2)
+  if (have && lam != mu && isfinite(lam)) {
+    const double dl = lam - mu;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) wv[r] = ga[r] - lam * gb[r] + dl * band_mv_m(y, r);
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x) y[r] = wv[r];
+    __syncthreads();
+    band_fwd(Lb, invD, y, N, bw);
+    band_back(Lb, invD, y, N, bw);
+  }
   // eigenvector c = [-y ; 1], scaled to b(u,u) = 1 and int u > 0
   double v[3] = {0.0, 0.0, 0.0};
   for (int r = threadIdx.x; r < N; r += blockDim.x) {
@@ -1040,7 +1053,10 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   }
   // y = S(mu)^{-1} w to the FP64 floor for the eigenvector; a stall with factors taken at
   // another shift refactors once (a stall at the same shift is the rounding floor)
-  if (have && !solve(mu, kFinalTarget) && sig != mu && factor(mu)) solve(mu, kFinalTarget);
+  // (at lambda, not at the last Newton iterate, so the eigenvector does not depend on where
+  // Newton stopped)
+  const double mfin = isfinite(lam) ? lam : mu;
+  if (have && !solve(mfin, kFinalTarget) && sig != mfin && factor(mfin)) solve(mfin, kFinalTarget);
   double v[3] = {0.0, 0.0, 0.0};
   for (int q = threadIdx.x; q < N; q += blockDim.x) {
     v[0] += y[q] * band_mv(MH, y, q);

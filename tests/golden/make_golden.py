@@ -2,7 +2,9 @@
 
 Calls only the CPU oracle (oracle/) on the seeded inputs of workloads/; nothing here
 comes from the CUDA path. Each file holds lambda_{h_k} for k = 1..n and u_{h_n} sampled
-on a coarse sub-lattice (every `stride`-th node in x and y).
+on a coarse sub-lattice (every `stride`-th node in x and y); the gradient file holds the
+oracle adjoint dlambda_{h_n}/dkappa on 20 seeded finest triangles, its maximum modulus and
+the Euler sum sum_e kappa_e g_e.
 
 Usage: python tests/golden/make_golden.py [name ...]
 """
@@ -36,11 +38,30 @@ def record(p, members, stride):
     return out
 
 
+def record_grad(p, n_el=20, seed=20):
+    from oracle import adjoint as AD
+
+    t = time.time()
+    g, lam = AD.grad_kappa(p, b=0)
+    rng = np.random.default_rng(seed)
+    ny, nx, _ = g.shape
+    els = []
+    while len(els) < n_el:  # elements inside the domain (kappa > 0)
+        j, i, tt = int(rng.integers(ny)), int(rng.integers(nx)), int(rng.integers(2))
+        if p.kappa[0, j, i, tt] > 0 and (j, i, tt) not in [e[:3] for e in els]:
+            els.append((j, i, tt, float(g[j, i, tt])))
+    out = {"problem": p.name, "lam": lam, "elements": els, "max_abs": float(np.abs(g).max()),
+           "euler_sum": float(np.sum(p.kappa[0] * g)), "oracle_seconds": time.time() - t}
+    print(p.name, "grad", lam, "%.1fs" % (time.time() - t), flush=True)
+    return out
+
+
 JOBS = {
     "c2": lambda: record(W.config2(), [0], 64),
     "c4": lambda: record(W.config4(), list(range(0, 256, 37)), 16),
     "c5": lambda: record(W.config5(), [0], 32),
     "c3n5": lambda: record(W.config3(levels=5), [0], 32),
+    "grad_c5": lambda: record_grad(W.config5()),
 }
 
 if __name__ == "__main__":
