@@ -205,8 +205,9 @@ def test_full_size_c5_adjoint_against_gpu_central_differences():
     truncation of up to ~3e-5 relative on some elements (the per-element derivative is small
     against its second-order change), so the difference is Richardson-extrapolated from h
     and h/2 (error O(h^4)), with h = 4e-3 kappa_e to keep the rounding part small. The
-    difference quotient needs lambda smooth in kappa at the 1e-14 level: the level-1 eigensolver stops on a residual test, and a different iteration
-    count moves u_{h_1} by about its tolerance, so it is converged to 1e-13 here (at the
+    difference quotient needs lambda smooth in kappa at the 1e-14 level: the level-1
+    eigensolver stops on a residual test, and a different iteration count moves u_{h_1} by
+    about its tolerance, so it is converged to 1e-13 here (at the
     default 1e-10 such jumps show up as ~1e-4 relative noise in the quotient). What remains
     is the FP64 rounding of lambda itself (~1e-14 relative), ~1e-10 absolute in the quotient:
     the bar is therefore 1e-5 of the gradient's scale max|g| for every sampled element, and
