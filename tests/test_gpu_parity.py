@@ -168,3 +168,20 @@ def test_fused_multigrid_matches_unfused(name, prec):
     # the root), which turns last-bit differences of u~ into ~1e-9 differences of u
     assert np.abs(u1.cpu().numpy() - u0.cpu().numpy()).max() <= 1e-7
     s.close()
+
+
+def test_lshape_eight_levels_converges_at_the_corner_rate():
+    """The 64-subdomain L-shape at its full 8 levels (12.6M unknowns; too large for the
+    oracle): lambda_{h_k} decreases with k, and successive differences shrink by ratios
+    that approach 2^{4/3} ~ 2.52 from above, the O(h^{4/3}) rate that the r^{2/3} singularity
+    of the first eigenfunction at the re-entrant corner allows (on the square the ratio is 4)."""
+    p = W.config3(levels=8)
+    lam, _, rep = _run(p, opts_for(1), want_u=False)
+    assert rep["status_flags"] == 0
+    lv = np.array(rep["lambda_levels"])
+    assert np.all(np.diff(lv) < 0)
+    d = -np.diff(lv)
+    ratios = d[:-1] / d[1:]
+    assert np.all(ratios > 2.4) and np.all(ratios < 3.2), ratios
+    assert ratios[-1] < ratios[0] and abs(ratios[-1] - 2.0 ** (4.0 / 3.0)) < 0.15, ratios
+    assert lam[0] == lv[-1]
