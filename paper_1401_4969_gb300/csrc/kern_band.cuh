@@ -137,130 +137,37 @@ __device__ inline void band_solve_shfl(const float* Ls, int ls, const float* inv
   __syncthreads();
 }
 
-// Row-blocked form of the FP32 factors for the T_H band (unknown r = (Y-1) b + (X-1),
-// b = ncx - 1 per grid row, half bandwidth b + 1): with that ordering L is block
-// lower-bidiagonal (the band profile of a first node in a row stops one grid row back, so
-// no fill reaches two blocks back). For nb = ncy - 1 blocks this stores, per block I, the
-// dense inverse of the unit lower triangular diagonal block (Dinv, rows r >= c) and the
-// sub-diagonal block Loff(r, c) = L(I b + r, (I - 1) b + c), each as a BS x BS tile padded
-// with zeros (BS >= b), so the solve can load whole rows without guards. Needs the scaled
-// factors Ls (L(i, i - d) = Ls[i * ls + d]).
-template <int BS>
-__device__ inline void band_blocks_f(const float* Ls, int ls, int bw, int b, int nb, float* Dinv, float* Loff) {
-  constexpr int T2 = BS * BS;
-  for (int q = threadIdx.x; q < nb * T2; q += blockDim.x) {
-    const int I = q / T2, rc = q - I * T2, r = rc / BS, c = rc - r * BS;
-    const int i = I * b + r, j = (I - 1) * b + c, d = i - j;
-    Loff[q] = (I > 0 && r < b && c < b && d >= 1 && d <= bw) ? Ls[i * ls + d] : 0.f;
-  }
-  // column c of the diagonal block's inverse: z_r = delta_rc - sum_{c <= k < r} L(r, k) z_k
-  for (int q = threadIdx.x; q < nb * BS; q += blockDim.x) {
-    const int I = q / BS, c = q - I * BS;
-    float* Z = Dinv + (long long)I * T2;
-    for (int r = 0; r < BS; ++r) {
-      float z = (r == c && c < b) ? 1.f : 0.f;
-      if (c < b && r < b && r > c)
-        for (int k = c; k < r; ++k) z -= Ls[(I * b + r) * ls + (r - k)] * Z[k * BS + c];
-      Z[r * BS + c] = (c < b && r < b && r >= c) ? z : 0.f;
-    }
-  }
-  __syncthreads();
-}
-
-// S x = y in place with the row-blocked factors: 2 nb block steps, each a b x b product
-// and a b x b triangular product, instead of 2 N dependent scalar steps. Run by warp 0
-// alone (b <= BS <= 32 lanes, one row of the block per lane) with warp barriers between
-// steps. y must be followed by BS readable finite floats and t (BS floats) zero beyond b;
-// the zero padding of the tiles cancels every out-of-block term.
-template <int BS>
-__device__ inline void band_solve_blocked(const float* Dinv, const float* Loff, const float* invD, float* y, float* t,
-                                          int b, int nb) {
-  if (threadIdx.x < 32) {
-    constexpr int T2 = BS * BS;
-    const int r = threadIdx.x;
-    for (int I = 0; I < nb; ++I) {
-      if (r < b) {
-        float s0 = y[I * b + r], s1 = 0.f;
-        if (I > 0) {
-          const float* Lo = Loff + (long long)I * T2 + r * BS;
-          const float* yp = y + (I - 1) * b;
-#pragma unroll
-          for (int c = 0; c < BS; c += 2) {
-            s0 -= Lo[c] * yp[c];
-            s1 -= Lo[c + 1] * yp[c + 1];
-          }
-        }
-        t[r] = s0 + s1;
-      }
-      __syncwarp();
-      if (r < b) {
-        const float* Z = Dinv + (long long)I * T2 + r * BS;
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int c = 0; c < BS; c += 2) {
-          s0 += Z[c] * t[c];
-          s1 += Z[c + 1] * t[c + 1];
-        }
-        y[I * b + r] = s0 + s1;
-      }
-      __syncwarp();
-    }
-    for (int q = r; q < nb * b; q += 32) y[q] *= invD[q];
-    __syncwarp();
-    for (int I = nb - 1; I >= 0; --I) {
-      if (r < b) {
-        float s0 = y[I * b + r], s1 = 0.f;
-        if (I + 1 < nb) {
-          const float* Lo = Loff + (long long)(I + 1) * T2;  // transpose: column r of block I + 1
-          const float* xn = y + (I + 1) * b;
-#pragma unroll
-          for (int c = 0; c < BS; c += 2) {
-            s0 -= Lo[c * BS + r] * xn[c];
-            s1 -= Lo[(c + 1) * BS + r] * xn[c + 1];
-          }
-        }
-        t[r] = s0 + s1;
-      }
-      __syncwarp();
-      if (r < b) {
-        const float* Z = Dinv + (long long)I * T2;  // transpose of the lower inverse
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int c = 0; c < BS; c += 2) {
-          s0 += Z[c * BS + r] * t[c];
-          s1 += Z[(c + 1) * BS + r] * t[c + 1];
-        }
-        y[I * b + r] = s0 + s1;
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-}
-
 // Block LDL^T of the T_H pencil S = K_H - mu M_H by grid rows (FP32), for unknowns ordered
 // r = (Y-1) b + (X-1): S is block tridiagonal with b x b diagonal blocks S_II (couplings
 // W/E) and sub-diagonal blocks S_{I,I-1} holding only the S and SW couplings (row r: columns
 // r and r - 1). With W_I = S_{I,I-1} P_{I-1}^{-1} and P_I = S_II - W_I S_{I,I-1}^T
 // (P_0 = S_00), S = L P L^T with L unit block lower bidiagonal (L_{I,I-1} = W_I) and P block
-// diagonal; the blocks are stored as BS x BS tiles (zero padded): Pinv[I] = P_I^{-1} and
-// W[I]. Sparse S_{I,I-1} makes W_I and P_I O(b^2) each; P_I is inverted by warp 0 alone
-// (Gauss-Jordan, row per lane, warp barriers). The band S(mu) (FP64, [r][d] = S(r, r-d))
-// is read from shared memory. `work` holds 2 BS x BS tiles. Returns false (to all threads)
-// if a pivot is not positive (S(mu) not positive definite); `flag` is a shared int.
+// diagonal; the blocks are stored as BS x BS tiles (zero padded) with row stride BS + 1
+// (blk_ld), so that a warp reading one row per lane or one column per lane hits 32
+// different shared-memory banks: Pinv[I] = P_I^{-1} and W[I]. Sparse S_{I,I-1} makes W_I
+// and P_I O(b^2) each; P_I is inverted by warp 0 alone (Gauss-Jordan with warp shuffles;
+// for BS = 16 lanes 0-15 reduce the rows of P_I and lanes 16-31 carry the rows of the
+// inverse). The band S(mu) (FP64, [r][d] = S(r, r-d)) is read from shared memory. `work`
+// holds 2 tiles. Returns false (to all threads) if a pivot is not positive (S(mu) not
+// positive definite); `flag` is a shared int.
+template <int BS>
+__host__ __device__ constexpr int blk_ld() { return BS + 1; }
+template <int BS>
+__host__ __device__ constexpr int blk_tile() { return BS * (BS + 1); }
+
 template <int BS>
 __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pinv, float* W, float* work, int* flag) {
-  constexpr int T2 = BS * BS;
+  constexpr int T2 = BS * BS, LD = blk_ld<BS>(), TS = blk_tile<BS>();
   const int tid = threadIdx.x, nt = blockDim.x;
-  float* A = work;        // P_I, inverted in place
-  float* Sub = work + T2; // dense copy of S_{I,I-1} (rows r: cols r, r-1)
+  float* A = work;        // P_I before inversion
+  float* Sub = work + TS; // dense copy of S_{I,I-1} (rows r: cols r, r-1)
   auto s_at = [&](int i, int j) -> float {  // S(i, j) for |i - j| <= bw from the band
     return i >= j ? (float)Sb[(long long)i * bw1 + (i - j)] : (float)Sb[(long long)j * bw1 + (j - i)];
   };
   if (tid == 0) *flag = 1;
   for (int I = 0; I < nb; ++I) {
-    const float* Pp = Pinv + (long long)(I - 1) * T2;
-    float* Wi = W + (long long)I * T2;
+    const float* Pp = Pinv + (long long)(I - 1) * TS;
+    float* Wi = W + (long long)I * TS;
     // S_{I,I-1} (two nonzeros per row) and W_I = S_{I,I-1} P_{I-1}^{-1}
     if (I > 0) {
       for (int q = tid; q < T2; q += nt) {
@@ -270,18 +177,18 @@ __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pi
           const int i = I * b + r, j = (I - 1) * b + c;
           if (c == r || c == r - 1) v = s_at(i, j);
         }
-        Sub[q] = v;
+        Sub[r * LD + c] = v;
       }
       __syncthreads();
       for (int q = tid; q < T2; q += nt) {
         const int r = q / BS, c = q % BS;
-        float v = Sub[r * BS + r] * Pp[r * BS + c];
-        if (r > 0) v += Sub[r * BS + r - 1] * Pp[(r - 1) * BS + c];
-        Wi[q] = (r < b && c < b) ? v : 0.f;
+        float v = Sub[r * LD + r] * Pp[r * LD + c];
+        if (r > 0) v += Sub[r * LD + r - 1] * Pp[(r - 1) * LD + c];
+        Wi[r * LD + c] = (r < b && c < b) ? v : 0.f;
       }
       __syncthreads();
     } else {
-      for (int q = tid; q < T2; q += nt) Wi[q] = 0.f;
+      for (int q = tid; q < T2; q += nt) Wi[(q / BS) * LD + q % BS] = 0.f;
     }
     // P_I = S_II - W_I S_{I,I-1}^T  ((S^T)_{kc} nonzero for k = c, c - 1... i.e. Sub[c][k], k in {c, c-1})
     for (int q = tid; q < T2; q += nt) {
@@ -291,53 +198,68 @@ __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pi
         const int i = I * b + r, j = I * b + c;
         if (r - c <= 1 && c - r <= 1) v = s_at(i, j);
         if (I > 0) {
-          v -= Wi[r * BS + c] * Sub[c * BS + c];
-          if (c > 0) v -= Wi[r * BS + c - 1] * Sub[c * BS + c - 1];
+          v -= Wi[r * LD + c] * Sub[c * LD + c];
+          if (c > 0) v -= Wi[r * LD + c - 1] * Sub[c * LD + c - 1];
         }
       } else if (r == c) {
         v = 1.f;  // padding: identity keeps the inverse's padding at zero off the diagonal
       }
-      A[q] = v;
+      A[r * LD + c] = v;
     }
     __syncthreads();
-    // Gauss-Jordan on A (symmetric positive definite): warp 0, lane = row
     if (tid < 32) {
-      float* Pi = Pinv + (long long)I * T2;
-      const int r = tid;
-      float row[BS], inv_row[BS];
-#pragma unroll
-      for (int c = 0; c < BS; ++c) {
-        row[c] = r < BS ? A[r * BS + c] : 0.f;
-        inv_row[c] = (r == c) ? 1.f : 0.f;
-      }
+      float* Pi = Pinv + (long long)I * TS;
+      const int lane = tid;
       int ok = 1;
+      if constexpr (BS == 16) {
+        // lane r < 16 holds row r of A, lane 16 + r row r of the inverse (starts as I)
+        const int r = lane & 15, hi = lane >> 4;
+        float v[BS];
 #pragma unroll
-      for (int k = 0; k < BS; ++k) {
-        const float pv = __shfl_sync(0xffffffffu, row[k], k);
-        if (!(pv > 0.f)) ok = 0;
-        const float ip = 1.0f / pv;
-        float prow[BS], pinv[BS];
+        for (int c = 0; c < BS; ++c) v[c] = hi ? (r == c ? 1.f : 0.f) : A[r * LD + c];
 #pragma unroll
-        for (int c = 0; c < BS; ++c) {
-          prow[c] = __shfl_sync(0xffffffffu, row[c], k) * ip;
-          pinv[c] = __shfl_sync(0xffffffffu, inv_row[c], k) * ip;
-        }
-        const float f = row[k];
+        for (int k = 0; k < BS; ++k) {
+          const float pv = __shfl_sync(0xffffffffu, v[k], k);
+          const float f = __shfl_sync(0xffffffffu, v[k], r);  // A(r, k) of the current step
+          if (!(pv > 0.f)) ok = 0;
+          const float ip = __frcp_rn(pv);
 #pragma unroll
-        for (int c = 0; c < BS; ++c) {
-          if (r == k) {
-            row[c] = prow[c];
-            inv_row[c] = pinv[c];
-          } else {
-            row[c] -= f * prow[c];
-            inv_row[c] -= f * pinv[c];
+          for (int c = 0; c < BS; ++c) {
+            const float pr = __shfl_sync(0xffffffffu, v[c], k + 16 * hi) * ip;
+            v[c] = (r == k) ? pr : v[c] - f * pr;
           }
         }
-      }
-      if (r < BS)
+        if (hi)
 #pragma unroll
-        for (int c = 0; c < BS; ++c) Pi[r * BS + c] = (r < b && c < b) ? inv_row[c] : 0.f;
-      if (r == 0 && !ok) *flag = 0;
+          for (int c = 0; c < BS; ++c) Pi[r * LD + c] = (r < b && c < b) ? v[c] : 0.f;
+      } else {
+        // one row per lane: row r of A and of its inverse
+        const int r = lane;
+        float row[BS], inv_row[BS];
+#pragma unroll
+        for (int c = 0; c < BS; ++c) {
+          row[c] = r < BS ? A[r * LD + c] : 0.f;
+          inv_row[c] = (r == c) ? 1.f : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < BS; ++k) {
+          const float pv = __shfl_sync(0xffffffffu, row[k], k);
+          if (!(pv > 0.f)) ok = 0;
+          const float ip = __frcp_rn(pv);
+          const float f = row[k];
+#pragma unroll
+          for (int c = 0; c < BS; ++c) {
+            const float pr = __shfl_sync(0xffffffffu, row[c], k) * ip;
+            const float pi = __shfl_sync(0xffffffffu, inv_row[c], k) * ip;
+            row[c] = (r == k) ? pr : row[c] - f * pr;
+            inv_row[c] = (r == k) ? pi : inv_row[c] - f * pi;
+          }
+        }
+        if (r < BS)
+#pragma unroll
+          for (int c = 0; c < BS; ++c) Pi[r * LD + c] = (r < b && c < b) ? inv_row[c] : 0.f;
+      }
+      if (lane == 0 && !ok) *flag = 0;
     }
     __syncthreads();
     if (!*flag) return false;
@@ -347,16 +269,16 @@ __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pi
 
 // S x = y in place with the block factors (L_{I,I-1} = W_I, P_I^{-1}): forward
 // u_I = y_I - W_I u_{I-1} (in place), backward x_I = P_I^{-1} u_I - W_{I+1}^T x_{I+1}, by
-// warp 0 (lane = row). y must be followed by BS readable finite floats; t is BS floats of
-// scratch.
+// warp 0 (lane = row; rows and columns of the padded tiles are conflict-free). y must be
+// followed by BS readable finite floats; t is BS floats of scratch.
 template <int BS>
 __device__ inline void block_solve_f(const float* Pinv, const float* W, float* y, float* t, int b, int nb) {
   if (threadIdx.x < 32) {
-    constexpr int T2 = BS * BS;
+    constexpr int LD = blk_ld<BS>(), TS = blk_tile<BS>();
     const int r = threadIdx.x;
     for (int I = 1; I < nb; ++I) {
       if (r < b) {
-        const float* Wr = W + (long long)I * T2 + r * BS;
+        const float* Wr = W + (long long)I * TS + r * LD;
         const float* up = y + (I - 1) * b;
         float s0 = y[I * b + r], s1 = 0.f;
 #pragma unroll
@@ -370,7 +292,7 @@ __device__ inline void block_solve_f(const float* Pinv, const float* W, float* y
     }
     for (int I = nb - 1; I >= 0; --I) {
       if (r < b) {
-        const float* Pr = Pinv + (long long)I * T2 + r * BS;
+        const float* Pr = Pinv + (long long)I * TS + r * LD;
         const float* u = y + I * b;
         float s0 = 0.f, s1 = 0.f;
 #pragma unroll
@@ -379,12 +301,12 @@ __device__ inline void block_solve_f(const float* Pinv, const float* W, float* y
           s1 += Pr[c + 1] * u[c + 1];
         }
         if (I + 1 < nb) {
-          const float* Wn = W + (long long)(I + 1) * T2;  // column r of W_{I+1}
+          const float* Wn = W + (long long)(I + 1) * TS;  // column r of W_{I+1}
           const float* xn = y + (I + 1) * b;
 #pragma unroll
           for (int c = 0; c < BS; c += 2) {
-            s0 -= Wn[c * BS + r] * xn[c];
-            s1 -= Wn[(c + 1) * BS + r] * xn[c + 1];
+            s0 -= Wn[c * LD + r] * xn[c];
+            s1 -= Wn[(c + 1) * LD + r] * xn[c + 1];
           }
         }
         t[r] = s0 + s1;

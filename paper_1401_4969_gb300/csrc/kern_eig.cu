@@ -827,11 +827,12 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   float* r32 = invD + N;                                    // N + 32 entries, the tail kept at 0
   const int bsz = bw - 1, nbk = bsz > 0 ? N / bsz : 0;     // row blocks (blocked solves)
   const int BS = bsz <= 16 ? 16 : 32;                      // padded tile edge
+  const int TS = BS * (BS + 1);                            // tile with row stride BS + 1
   float* Dinv = r32 + N + 32;
-  float* Loff = Dinv + (a.blocked ? (long long)nbk * BS * BS : 0);
-  float* tb = Loff + (a.blocked ? (long long)nbk * BS * BS : 0);
-  float* bwork = tb + (a.blocked ? BS : 0);                // 2 BS x BS tiles (block factorisation)
-  int* pairs = reinterpret_cast<int*>(a.smem ? bwork + (a.blocked ? 2 * BS * BS : 0) : reinterpret_cast<float*>(rr_sm));
+  float* Loff = Dinv + (a.blocked ? (long long)nbk * TS : 0);
+  float* tb = Loff + (a.blocked ? (long long)nbk * TS : 0);
+  float* bwork = tb + (a.blocked ? BS : 0);                // 2 tiles (block factorisation)
+  int* pairs = reinterpret_cast<int*>(a.smem ? bwork + (a.blocked ? 2 * TS : 0) : reinterpret_cast<float*>(rr_sm));
   if (a.smem) {
     for (int q = threadIdx.x; q < 32; q += blockDim.x) r32[N + q] = 0.f;
     if (a.blocked)
@@ -1089,7 +1090,8 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
 // vectors, the row-blocked factors (blocked mode) and the pair table.
 size_t rr_mixed_smem_bytes(int nhb, int bw, int blocked) {
   const size_t bsz = bw - 1, bs = bsz <= 16 ? 16 : 32;
-  const size_t blk = blocked && bsz > 0 ? 2 * (nhb / bsz) * bs * bs + bs + 2 * bs * bs : 0;
+  const size_t ts = bs * (bs + 1);  // padded tile
+  const size_t blk = blocked && bsz > 0 ? 2 * (nhb / bsz) * ts + bs + 2 * ts : 0;
   return (size_t)nhb * 5 * 8 + 3 * (size_t)nhb * (bw + 1) * 8 +
          ((size_t)nhb * (bw + 1) + 2 * (size_t)nhb + 32 + blk + 2) * 4 + (size_t)(bw * (bw + 1) / 2) * 4 + 16;
 }
