@@ -68,7 +68,9 @@ typedef struct mlev_opts {
   int post_smooth;      /* sweeps after prolongation */
   int coarse_sweeps;    /* sweeps on the coarsest grid of each multigrid hierarchy */
   int level1_max_iter;  /* iteration cap of the level-1 eigensolver (Algorithm 4.2 step 1) */
-  double level1_tol;    /* relative eigen-residual target of the level-1 eigensolver */
+  double level1_tol;    /* relative eigen-residual target of the level-1 eigensolver; the
+                           correction steps contract its error, so the autotuner may loosen
+                           it (mlev_grad_kappa's forward pass uses at most 1e-10) */
   int rr_max_iter;      /* Newton/bisection cap of the Rayleigh-Ritz step */
   int use_graph;        /* 1: capture the launch sequence in a CUDA graph and replay it */
   double omega;         /* over-relaxation of the red-black Gauss-Seidel smoother (1 = plain GS) */
@@ -228,7 +230,9 @@ int mlev_profile_read(mlev_ctx* ctx, mlev_kernel_stat* out, int capacity, int* c
  * The map differentiated is the algorithm itself, every local and G_{m+1} solve
  * (Eqs. Aux_Problem, G_m+1_Problem) and both eigenproblems (Algorithm 4.2 step 1,
  * Eq. Eigen_Augment_Problem) taken as exact; the discrete solves use the same
- * multigrid, precision and cycle counts as mlev_solve with the same opts. The call
+ * multigrid, precision and cycle counts as mlev_solve with the same opts, except that
+ * level 1 is solved to a relative residual of at most 1e-10 (opts.level1_tol is capped
+ * there, since the level-1 adjoint needs the exact level-1 eigenpair). The call
  * runs the forward solve again (keeping u~_k, lambda_k and the Rayleigh-Ritz
  * coefficients of every level), then the reverse sweep, in which the local solutions
  * e^j of each level are recomputed rather than stored.

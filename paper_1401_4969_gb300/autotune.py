@@ -10,8 +10,10 @@ coefficient). The tuner measures it on the device:
    member's eigenvalue is within `safety * target_rel` of the reference,
 3. a staged search: first the cycle counts (vcycles, refine_passes, strip_vcycles) in
    increasing order of work, then the smoothing sweeps and coarsest-grid sweeps of the
-   cheapest accepted schedule, then the size of the one-block tail of the fused V-cycle
-   and the fused / unfused multigrid kernels.
+   cheapest accepted schedule, then the residual target of the level-1 eigensolver (each
+   correction step of Algorithm 4.1 contracts the error of the previous level's
+   eigenvector, so level 1 need not be solved to rounding), then the size of the one-block
+   tail of the fused V-cycle and the fused / unfused multigrid kernels.
 
 The fastest accepted schedule is cached in a JSON file keyed by the problem's signature,
 the precision, the target and the device name.
@@ -26,7 +28,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 TUNE_KEYS = ("vcycles", "refine_passes", "strip_vcycles", "pre_smooth", "post_smooth", "coarse_sweeps", "fused",
-             "tail_nodes")
+             "tail_nodes", "level1_tol")
+FLOAT_KEYS = ("level1_tol",)
+LEVEL1_TOLS = (1e-8, 1e-6, 1e-4, 1e-3)  # level-1 residual targets tried, tightest first
 
 
 def default_cache_path() -> str:
@@ -91,8 +95,10 @@ def search(evaluate, target_rel: float, safety: float = 0.1, base: dict | None =
 
     Stage 1 walks the cycle candidates in increasing work and stops after `max_accept`
     accepted schedules; stage 2 lowers the smoothing and coarsest sweeps of the fastest
-    accepted one; stage 3 compares the fused and unfused multigrid kernels."""
-    base = dict(base or {"pre_smooth": 2, "post_smooth": 2, "coarse_sweeps": 40, "fused": 1, "tail_nodes": 0})
+    accepted one and loosens the level-1 residual target; stage 3 compares the fused and
+    unfused multigrid kernels."""
+    base = dict(base or {"pre_smooth": 2, "post_smooth": 2, "coarse_sweeps": 40, "fused": 1, "tail_nodes": 0,
+                         "level1_tol": 1e-10})
     tol = safety * target_rel
     trials: list[Trial] = []
 
@@ -113,7 +119,8 @@ def search(evaluate, target_rel: float, safety: float = 0.1, base: dict | None =
         raise RuntimeError(f"no schedule reached relative error {tol:g}; best trials: "
                            f"{sorted(trials, key=lambda t: t.err)[:3]}")
     best = min(accepted, key=lambda t: t.ms)
-    for key, values in (("coarse_sweeps", (20, 10)), ("pre_smooth", (1,)), ("post_smooth", (1,))):
+    for key, values in (("coarse_sweeps", (20, 10)), ("pre_smooth", (1,)), ("post_smooth", (1,)),
+                        ("level1_tol", LEVEL1_TOLS)):
         for v in values:
             t = run({**best.opts, key: v})
             if t.ok and t.ms < best.ms:
@@ -204,5 +211,5 @@ def tune(problem, precision: int = 1, target_rel: float = 1e-8, device: int = 0,
 def apply(opts_struct, tuned: dict):
     """Copy a tuned schedule into an mlev Opts structure."""
     for k, v in tuned.items():
-        setattr(opts_struct, k, int(v))
+        setattr(opts_struct, k, float(v) if k in FLOAT_KEYS else int(v))
     return opts_struct

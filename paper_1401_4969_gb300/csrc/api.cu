@@ -893,10 +893,17 @@ int solve_impl(mlev_ctx* ctx, const mlev_opts* o, void* ws, size_t ws_bytes, cud
   return rc;
 }
 
+constexpr double kGradLevel1Tol = 1e-10;
+
 int grad_impl(mlev_ctx* ctx, const mlev_opts* o, void* ws, cudaStream_t s, const double* kappa_src,
               const double* dl, int layout, double* dkappa, double* lambda_out) {
   const Plan& P = ctx->plan;
-  Launcher ln{ctx, P, *o, ws, s};
+  // the reverse sweep differentiates an exact level-1 eigenpair (its projected adjoint solve
+  // needs u_{h_1} to satisfy the level-1 pencil), so the forward pass solves level 1 to at
+  // least kGradLevel1Tol whatever the caller's schedule asks
+  mlev_opts og = *o;
+  og.level1_tol = std::min(og.level1_tol, kGradLevel1Tol);
+  Launcher ln{ctx, P, og, ws, s};
   ln.kappa_src = kappa_src;
   std::vector<ProfRec> recs;
   if (o->profile) {

@@ -10,8 +10,9 @@ def _model(o):
     """Synthetic cost/accuracy model: error falls geometrically with cycles, time grows with them."""
     cyc = o["vcycles"] * o["refine_passes"]
     scyc = o["strip_vcycles"] * o["refine_passes"]
-    err = 1e-3 * 0.03 ** min(cyc, scyc + 1) * (3.0 if o["pre_smooth"] == 1 else 1.0)
-    ms = 1.0 + 0.5 * cyc + 0.3 * scyc + 0.01 * o["coarse_sweeps"] + 0.2 * o["pre_smooth"] + (0.4 if not o["fused"] else 0)
+    err = 1e-3 * 0.03 ** min(cyc, scyc + 1) * (3.0 if o["pre_smooth"] == 1 else 1.0) + 1e-3 * o["level1_tol"]
+    ms = (1.0 + 0.5 * cyc + 0.3 * scyc + 0.01 * o["coarse_sweeps"] + 0.2 * o["pre_smooth"] + (0.4 if not o["fused"] else 0)
+          - 0.05 * np.log10(o["level1_tol"]))
     return ms, err
 
 
@@ -23,6 +24,21 @@ def test_search_picks_the_fastest_schedule_within_target():
     # no accepted trial is faster than the result
     assert min(t.ms for t in res.trials if t.ok) == pytest.approx(res.ms)
     assert res.opts["fused"] == 1 and res.opts["coarse_sweeps"] == 10
+    # the level-1 target was loosened, and the next looser candidate broke the bar
+    chosen = res.opts["level1_tol"]
+    assert chosen in AT.LEVEL1_TOLS
+    i = AT.LEVEL1_TOLS.index(chosen)
+    if i + 1 < len(AT.LEVEL1_TOLS):
+        looser = [t for t in res.trials if t.opts["level1_tol"] == AT.LEVEL1_TOLS[i + 1]]
+        assert looser and not any(t.ok for t in looser)
+
+
+def test_apply_keeps_float_keys():
+    class O:
+        pass
+
+    o = AT.apply(O(), {"vcycles": 2.0, "level1_tol": 1e-6})
+    assert o.vcycles == 2 and isinstance(o.vcycles, int) and o.level1_tol == 1e-6
 
 
 def test_search_raises_when_nothing_meets_the_target():
