@@ -24,6 +24,7 @@ struct ProfRecHost {
 
 struct mlev_ctx {
   int device = 0;
+  int sm_count = 0, smem_per_sm = 0;  // device attributes (launch-shape decisions)
   Plan plan;
   std::string err;
   // plan tables are (re)uploaded when the workspace, the plan or the options change
@@ -437,6 +438,41 @@ struct Launcher {
       a.c0 = c0L(L - 1);
       a.lam = lam;
       a.lam_stride = n + 1;
+      RRArgs rr{};
+      rr.B = B;
+      rr.L = L;
+      rr.n = n;
+      rr.nhb = P.nhb;
+      rr.bw = P.bw;
+      rr.KH = KH;
+      rr.MH = MH;
+      rr.chol = at<double>(ws, P.w_chol);
+      rr.partials = partials;
+      rr.lam = lam;
+      rr.c = cL(L);
+      rr.c0 = c0L(L);
+      rr.c_prev = cL(L - 1);
+      rr.c0_prev = c0L(L - 1);
+      rr.stat = stat;
+      rr.stat_stride = stat_stride;
+      rr.max_iter = o.rr_max_iter;
+      rr.mixed = (mixed && rr_mixed_supported(P.nhb, P.bw)) ? 1 : 0;
+      // row-blocked solves: one warp holds a grid row of the coarse system (<= 32 nodes)
+      rr.blocked = rr.mixed && P.bw - 1 <= 32 && rr_mixed_smem_bytes(P.nhb, P.bw, 1) <= (size_t)kRRSmemMax ? 1 : 0;
+      rr.smem = (rr.mixed ? rr_mixed_smem_bytes(P.nhb, P.bw, rr.blocked) : rr_smem_bytes(P.nhb, P.bw)) <=
+                (size_t)kRRSmemMax;
+      // the Rayleigh-Ritz factors of this level are prepared by the inner-product kernel
+      // (they need only K_H, M_H and the eigenvalues of the earlier levels)
+      rr.pre = at<unsigned char>(ws, P.w_rrpre);
+      rr.pre_stride = (long long)mlev_rr_prefactor_stride(P.nhb, P.bw);
+      // only where the inner-product kernel, every block then holding the factor's shared
+      // memory, still runs in one wave (a batch of many problems would lose occupancy there)
+      const size_t pre_smem = rr_prefactor_smem(P.nhb, P.bw);
+      const long long aug_blocks = (long long)B * (P.ncx * P.ncy + 1);
+      const long long aug_slots = (long long)ctx->sm_count * (long long)(ctx->smem_per_sm / (pre_smem + 1024));
+      rr.use_pre = rr.blocked && rr.smem && L >= 4 && P.w_rrpre.bytes > 0 && pre_smem <= (size_t)kRRSmemMax &&
+                           aug_blocks <= aug_slots ? 1 : 0;
+      const RRPrefactor pf{KH, MH, P.nhb, P.bw, rr.pre, rr.pre_stride};
       go(F_INTERP, 10.0 * nfree, [&] { launch_interp(G, P.glay, a, s); });
       go(F_RHS, (16.0 + kfine_extra()) * nfree, [&] { launch_rhs(G, P.glay, a, s); });
       // multigrid pools of this level start at zero: nodes that are not unknowns must read
@@ -475,30 +511,8 @@ struct Launcher {
            [&] { launch_strip_update(G, P.glay, a, tiles_at(stop), stop.count, E, mixed ? 1 : 0, s); });
       }
       // step 3: Rayleigh-Ritz on V_{0H} + span{u~}
-      go(F_AUG, (8.0 + kfine_extra()) * nfree, [&] { launch_aug(G, P.glay, a, partials, s); });
-      RRArgs rr{};
-      rr.B = B;
-      rr.L = L;
-      rr.n = n;
-      rr.nhb = P.nhb;
-      rr.bw = P.bw;
-      rr.KH = KH;
-      rr.MH = MH;
-      rr.chol = at<double>(ws, P.w_chol);
-      rr.partials = partials;
-      rr.lam = lam;
-      rr.c = cL(L);
-      rr.c0 = c0L(L);
-      rr.c_prev = cL(L - 1);
-      rr.c0_prev = c0L(L - 1);
-      rr.stat = stat;
-      rr.stat_stride = stat_stride;
-      rr.max_iter = o.rr_max_iter;
-      rr.mixed = (mixed && rr_mixed_supported(P.nhb, P.bw)) ? 1 : 0;
-      // row-blocked solves: one warp holds a grid row of the coarse system (<= 32 nodes)
-      rr.blocked = rr.mixed && P.bw - 1 <= 32 && rr_mixed_smem_bytes(P.nhb, P.bw, 1) <= (size_t)kRRSmemMax ? 1 : 0;
-      rr.smem = (rr.mixed ? rr_mixed_smem_bytes(P.nhb, P.bw, rr.blocked) : rr_smem_bytes(P.nhb, P.bw)) <=
-                (size_t)kRRSmemMax;
+      go(F_AUG, (8.0 + kfine_extra()) * nfree,
+         [&] { launch_aug(G, P.glay, a, partials, rr.use_pre ? &pf : nullptr, s); });
       go(F_RR, 0.0, [&] { launch_rr(G, rr, s); });
     }
     go(F_OUT, 16.0 * B, [&] { launch_lambda_out(B, n, lam, lambda_out, s); });
@@ -576,7 +590,7 @@ struct Launcher {
       // u_in and r of the forward level (cheap to recompute), inner products of u~_L
       go(F_INTERP, 10.0 * nfree, [&] { launch_interp(G, P.glay, a, s); });
       go(F_RHS, (16.0 + kfine_extra()) * nfree, [&] { launch_rhs(G, P.glay, a, s); });
-      go(F_AUG, (8.0 + kfine_extra()) * nfree, [&] { launch_aug(G, P.glay, a, partials, s); });
+      go(F_AUG, (8.0 + kfine_extra()) * nfree, [&] { launch_aug(G, P.glay, a, partials, nullptr, s); });
       // Rayleigh-Ritz adjoint
       go(F_ADJ_FIELD, 16.0 * nfree, [&] { launch_cbar(G, P.glay, L, B, utl, ubL, part2, s); });
       RRAdjArgs ra{};
@@ -975,7 +989,9 @@ int mlev_create(mlev_ctx** out, int device) {
   mlev_ctx* c = new (std::nothrow) mlev_ctx();
   if (!c) return MLEV_ENOMEM;
   c->device = device;
-  if (cudaSetDevice(device) != cudaSuccess) {
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess) {
     delete c;
     return MLEV_ECUDA;
   }

@@ -319,4 +319,48 @@ __device__ inline void block_solve_f(const float* Pinv, const float* W, float* y
   __syncthreads();
 }
 
+
+// Factors of S(sigma) = K_H - sigma M_H for the Rayleigh-Ritz step of level L, prepared by
+// one block of the inner-product kernel of the same level (which runs just before the
+// Rayleigh-Ritz kernel and reads neither input nor output of this). sigma extrapolates the
+// eigenvalues of the earlier levels: with d1 = lambda_{L-2} - lambda_{L-1} and
+// d2 = lambda_{L-3} - lambda_{L-2} the differences shrink by r = d2 / d1 per level, so
+// lambda_L ~ lambda_{L-1} - d1 / r. Only a regular sequence (2 <= r <= 8, as for the O(h^2)
+// and corner-limited rates) is used; the Rayleigh-Ritz kernel refines against these
+// factors and refactors at its own mu if the refinement stalls. `out` holds the layout of
+// mlev_rr_prefactor_stride; `sm` is dynamic shared memory of rr_prefactor_smem bytes.
+// Called by all threads of the block.
+__device__ inline void rr_prefactor_block(const double* KH, const double* MH, const double* lamp, int L, int nhb,
+                                          int bw, unsigned char* out, double* sm, int* flag) {
+  const int N = nhb, bw1 = bw + 1, bsz = bw - 1, nbk = N / bsz;
+  double sigma = NAN;
+  bool use = L >= 4;
+  if (use) {
+    const double l1 = lamp[L - 1], l2 = lamp[L - 2], l3 = lamp[L - 3];
+    const double d1 = l2 - l1, d2 = l3 - l2;
+    const double r = d2 / d1;
+    use = d1 > 0.0 && d2 > 0.0 && r >= 2.0 && r <= 8.0;
+    sigma = l1 - d1 / r;
+  }
+  if (!use) {
+    if (threadIdx.x == 0) *reinterpret_cast<int*>(out + 8) = 0;
+    return;
+  }
+  const int BS = bsz <= 16 ? 16 : 32, TS = BS * (BS + 1);
+  double* sb = sm;                                                   // S(sigma), FP64 band
+  float* tiles = reinterpret_cast<float*>(sb + (long long)N * bw1);  // P_I^{-1} tiles, then W_I
+  float* work = tiles + 2LL * nbk * TS;
+  for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) sb[q] = KH[q] - sigma * MH[q];
+  __syncthreads();
+  const bool ok = BS == 16 ? block_ldlt_f<16>(sb, bw1, bsz, nbk, tiles, tiles + (long long)nbk * TS, work, flag)
+                           : block_ldlt_f<32>(sb, bw1, bsz, nbk, tiles, tiles + (long long)nbk * TS, work, flag);
+  float* dst = reinterpret_cast<float*>(out + 16);
+  if (ok)
+    for (long long q = threadIdx.x; q < 2LL * nbk * TS; q += blockDim.x) dst[q] = tiles[q];
+  if (threadIdx.x == 0) {
+    *reinterpret_cast<double*>(out) = sigma;
+    *reinterpret_cast<int*>(out + 8) = ok ? 1 : 0;
+  }
+}
+
 }  // namespace mlev

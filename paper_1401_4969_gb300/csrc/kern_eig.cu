@@ -1011,6 +1011,17 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   double mu = alpha / beta, lo = 0.0, hi = INFINITY, lam = NAN;
   int it = 0, status = 0;
   bool have = false, factored = false;
+  if (a.use_pre && a.blocked && a.smem) {
+    // factors of S(sigma) prepared while this level's local problems ran (k_rr_prefactor)
+    const unsigned char* pp = a.pre + (long long)p * a.pre_stride;
+    if (*reinterpret_cast<const int*>(pp + 8)) {
+      const float* src = reinterpret_cast<const float*>(pp + 16);
+      for (long long q = threadIdx.x; q < 2LL * nbk * TS; q += blockDim.x) Dinv[q] = src[q];
+      sig = *reinterpret_cast<const double*>(pp);
+      factored = true;
+    }
+    __syncthreads();
+  }
   for (; it < a.max_iter; ++it) {
     bool ok = factored && solve(mu, kNewtonTarget);
     if (!ok) {
@@ -1084,6 +1095,13 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     if (!isfinite(lam) || !isfinite(sc)) status |= MLEV_ST_NONFINITE;
     if (status) atomicOr((unsigned long long*)&a.stat[p * a.stat_stride + MLEV_STAT_FLAGS], (unsigned long long)status);
   }
+}
+
+size_t rr_prefactor_smem(int nhb, int bw) {
+  const int bsz = bw - 1;
+  if (bsz <= 0 || bsz > 32) return (size_t)-1;
+  const size_t bs = bsz <= 16 ? 16 : 32;
+  return (size_t)nhb * (bw + 1) * 8 + (2 * (size_t)(nhb / bsz) + 2) * bs * (bs + 1) * 4;
 }
 
 // Shared memory of k_rr_mixed: 5 FP64 vectors, K_H, M_H and S(mu), the FP32 band, 2 FP32

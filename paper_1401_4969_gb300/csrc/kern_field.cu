@@ -2,6 +2,7 @@
 // u_{h_k} into V_{h_{k+1}}, the right-hand side of the auxiliary problems, the
 // gluing of step 2, the G_{m+1} right-hand side, the inner products of step 3,
 // and set-up kernels for kappa and the coarse matrices.
+#include "kern_band.cuh"
 #include "kern_coarse.cuh"
 #include "kern_launch.h"
 
@@ -123,11 +124,27 @@ __global__ void __launch_bounds__(256) k_strip_update(DevGeom G, GlobalLayout gl
 // and the cell's share of g_a = P_H^T K u~, g_b = P_H^T M u~ at its four corners.
 // partials[p][cell][12]: 0 alpha, 1 beta, 2 sigma, 3..6 K-part at corners 00,10,01,11,
 // 7..10 M-part at corners 00,10,01,11.
-template <int KK>
-__global__ void __launch_bounds__(256) k_aug(DevGeom G, GlobalLayout gl, LevelArgs a, double* partials) {
+template <int KK, bool PRE>
+__global__ void __launch_bounds__(256) k_aug(DevGeom G, GlobalLayout gl, LevelArgs a, double* partials,
+                                             RRPrefactor pf) {
+  extern __shared__ double aug_dyn[];
   __shared__ double scratch[8 * 11];
   __shared__ double outv[11];
-  const int ci = blockIdx.x, cj = blockIdx.y, p = blockIdx.z, L = a.L;
+  __shared__ int pflag;
+  // with PRE, blocks [0, B) prepare the Rayleigh-Ritz factors (first, so they start first),
+  // then one block per coarse cell of each batch member (a separate instantiation, so the
+  // plain kernel keeps its default shared-memory configuration)
+  const long long npre = PRE ? a.B : 0;
+  if (PRE && (long long)blockIdx.x < npre) {
+    const int p = blockIdx.x;
+    const long long band = (long long)pf.nhb * (pf.bw + 1);
+    rr_prefactor_block(pf.KH + p * band, pf.MH + p * band, a.lam + (long long)p * a.lam_stride, a.L, pf.nhb, pf.bw,
+                       pf.out + p * pf.stride, aug_dyn, &pflag);
+    return;
+  }
+  const long long q = (long long)blockIdx.x - npre;
+  const int ncell = G.ncx * G.ncy;
+  const int p = (int)(q / ncell), ci = (int)(q % ncell) % G.ncx, cj = (int)(q % ncell) / G.ncx, L = a.L;
   double acc[11];
 #pragma unroll
   for (int k = 0; k < 11; ++k) acc[k] = 0.0;
@@ -299,8 +316,24 @@ void launch_strip_update(const DevGeom& G, const GlobalLayout& gl, const LevelAr
   if (!n) return;
   k_strip_update<<<n, dim3(GX, GY), 0, s>>>(G, gl, a, tiles, E, use64);
 }
-void launch_aug(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, double* partials, cudaStream_t s) {
-  MLEV_DISPATCH_KK(G.kap.kind, (k_aug<KK><<<dim3(G.ncx, G.ncy, a.B), 256, 0, s>>>(G, gl, a, partials)));
+template <int KK>
+static void launch_aug_kk(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, double* partials,
+                          const RRPrefactor* pf, cudaStream_t s) {
+  if (!pf) {
+    k_aug<KK, false><<<(unsigned)((long long)a.B * G.ncx * G.ncy), 256, 0, s>>>(G, gl, a, partials, RRPrefactor{});
+    return;
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_aug<KK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRRSmemMax);
+    attr = true;
+  }
+  const long long nb = (long long)a.B * (G.ncx * G.ncy + 1);
+  k_aug<KK, true><<<(unsigned)nb, 256, rr_prefactor_smem(pf->nhb, pf->bw), s>>>(G, gl, a, partials, *pf);
+}
+void launch_aug(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, double* partials, const RRPrefactor* pf,
+                cudaStream_t s) {
+  MLEV_DISPATCH_KK(G.kap.kind, (launch_aug_kk<KK>(G, gl, a, partials, pf, s)));
 }
 void launch_output_u(const DevGeom& G, const GlobalLayout& gl, int L, int B, const double* ut, const double* c,
                      const double* c0, double* u_out, cudaStream_t s) {

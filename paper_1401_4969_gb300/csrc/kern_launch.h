@@ -72,7 +72,17 @@ void launch_strip_rhs(const DevGeom& G, const GlobalLayout& gl, const LevelArgs&
                       T* F, double* X64, cudaStream_t s);
 void launch_strip_update(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const Tile* tiles, int n,
                          const double* E, int use64, cudaStream_t s);
-void launch_aug(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, double* partials, cudaStream_t s);
+// Rayleigh-Ritz factors prepared by one extra block per batch member of the inner-product
+// kernel (rr_prefactor_block); K_H, M_H [B][nhb][bw+1], out [B][stride].
+struct RRPrefactor {
+  const double* KH;
+  const double* MH;
+  int nhb, bw;
+  unsigned char* out;
+  long long stride;
+};
+void launch_aug(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, double* partials,
+                const RRPrefactor* pf, cudaStream_t s);  // pf nullable
 void launch_output_u(const DevGeom& G, const GlobalLayout& gl, int L, int B, const double* ut, const double* c,
                      const double* c0, double* u_out, cudaStream_t s);
 void launch_kappa_copy_fine(const KappaDev& kv, int n, int B, const double* src, double* lvl, float* lvl_f,
@@ -128,8 +138,12 @@ struct RRArgs {
   const double* c_prev;  // coefficients of u_{h_k} (the previous level's eigenvector): warm start
   const double* c0_prev;
   int blocked;           // 1: row-blocked FP32 solves (needs smem), else the warp solve
+  unsigned char* pre;    // [B][pre_stride] factors of S(sigma) prepared ahead (mlev_rr_prefactor_stride)
+  long long pre_stride;
+  int use_pre;           // k_rr_mixed starts from the prepared factors when their flag is set
 };
 void launch_rr(const DevGeom& G, const RRArgs& a, cudaStream_t s);
+size_t rr_prefactor_smem(int nhb, int bw);  // shared memory of rr_prefactor_block
 size_t rr_smem_bytes(int nhb, int bw);
 size_t rr_mixed_smem_bytes(int nhb, int bw, int blocked);
 int rr_mixed_supported(int nhb, int bw);

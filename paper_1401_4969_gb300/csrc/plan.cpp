@@ -542,6 +542,7 @@ std::string Plan::build(const mlev_opts& o) {
   take(w_stat, (size_t)B * mlev_stat_stride(n) * 8);
   take(w_jobnorm, (size_t)B * (m + 1) * 2 * 8);
   take(w_chol, (size_t)B * ((size_t)nhb * (bw + 1) + 5 * (size_t)nhb) * 8);
+  take(w_rrpre, tsize == 4 ? (size_t)B * mlev_rr_prefactor_stride(nhb, bw) : 0);
   take(w_out_lam, (size_t)B * 8);
   take(w_out_u, (size_t)B * (lvl_nx(n) + 1) * (lvl_ny(n) + 1) * 8);
   take(w_cinv, sub_direct ? (size_t)B * m * nd_max * nd_max * tsize : 0);

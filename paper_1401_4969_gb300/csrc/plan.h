@@ -94,6 +94,7 @@ struct Plan {
   Span w_grids, w_tiles, w_regions, w_qlabel, w_cellin, w_subtop;
   Span w_kstage, w_klvl, w_klvl_f, w_kcf, w_band, w_ut[2], w_uin, w_r, w_l1vec, w_l1pool[2];
   Span w_x, w_f, w_x64, w_aug, w_lam, w_c, w_c0, w_stat, w_jobnorm, w_chol, w_out_lam, w_out_u, w_cinv, w_tmaps;
+  Span w_rrpre;  // Rayleigh-Ritz factors prepared ahead of a level (mixed precision only)
   size_t ws_bytes = 0;
   size_t tables_bytes = 0;
   // adjoint (mlev_grad_kappa): extra regions after the solve's, up to ws_grad_bytes
