@@ -430,6 +430,10 @@ struct Launcher {
       LevelArgs a{};
       a.L = L;
       a.B = B;
+      {
+        const double h = P.H / (double)(1 << L);  // exact: the kernels' h_L
+        a.m12 = h * h / 12.0;
+      }
       a.ut_prev = utL(L - 1);
       a.ut = utL(L);
       a.uin = uin;
@@ -579,6 +583,10 @@ struct Launcher {
       LevelArgs a{};
       a.L = L;
       a.B = B;
+      {
+        const double h = P.H / (double)(1 << L);  // exact: the kernels' h_L
+        a.m12 = h * h / 12.0;
+      }
       a.ut_prev = ck_ut + (size_t)(k - 1) * gfield;
       a.ut = utl;
       a.uin = uin;

@@ -10,8 +10,8 @@ namespace mlev {
 __device__ __forceinline__ double coarse_eval(const DevGeom& G, const double* c, int L, int i, int j) {
   const int ci = min(i >> L, G.ncx - 1), cj = min(j >> L, G.ncy - 1);
   const int ri = i - (ci << L), rj = j - (cj << L);
-  const double S = (double)(1 << L);
-  const double s = ri / S, t = rj / S;
+  const double invS = pow2(-L);  // ri / 2^L exactly
+  const double s = ri * invS, t = rj * invS;
   const int w = G.ncx + 1;
   const double c00 = c[cj * w + ci], c11 = c[(cj + 1) * w + ci + 1];
   if (ri >= rj) return c00 * (1.0 - s) + c[cj * w + ci + 1] * (s - t) + c11 * t;  // lower triangle

@@ -176,7 +176,11 @@ __device__ __forceinline__ V apply_m12(const T* x, long long c, int pitch) {
          (V)x[c - pitch - 1];
 }
 
-__device__ __forceinline__ double level_h(double H, int l) { return l >= 0 ? H / (double)(1 << l) : H * (double)(1 << (-l)); }
+// 2^e as a double, built from its exponent field (exact for |e| < 1023): scaling by it equals
+// dividing by 2^-e bit for bit, without an FP64 division.
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+__device__ __forceinline__ double level_h(double H, int l) { return H * pow2(-l); }
 
 // Block-wide sum of NV doubles per thread into sh[0..NV-1] (deterministic tree order).
 // `scratch` holds blockDim.x/32 * NV doubles. All threads must call it.

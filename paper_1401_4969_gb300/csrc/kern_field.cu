@@ -50,11 +50,10 @@ __global__ void __launch_bounds__(256) k_rhs(DevGeom G, GlobalLayout gl, LevelAr
     a.r[base + c] = 0.0;
     return;
   }
-  const double h = level_h(G.H, L);
   const double lam = a.lam[p * a.lam_stride + (L - 1)];
   const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
   const double* u = a.uin + base;
-  a.r[base + c] = lam * (h * h / 12.0) * apply_m12<double, double>(u, c, pitch) - apply_k<double, double>(u, c, pitch, w);
+  a.r[base + c] = lam * a.m12 * apply_m12<double, double>(u, c, pitch) - apply_k<double, double>(u, c, pitch, w);
 }
 
 // Step 2 of Algorithm 4.1: u~ = u_in + e^j on closed G_j, u_in on G_{m+1} (corrected
@@ -101,10 +100,9 @@ __global__ void __launch_bounds__(256) k_strip_rhs(DevGeom G, GlobalLayout gl, L
   }
   const int L = g.level, p = g.problem, pitch = gl.pitch[lidx(L)];
   const long long base = (long long)p * gl.bstride, gc = (long long)j * pitch + i;
-  const double h = level_h(G.H, L);
   const double lam = a.lam[p * a.lam_stride + (L - 1)];
   const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
-  const double r = lam * (h * h / 12.0) * apply_m12<double, double>(a.uin + base, gc, pitch) -
+  const double r = lam * a.m12 * apply_m12<double, double>(a.uin + base, gc, pitch) -
                    apply_k<double, double>(a.ut + base, gc, pitch, w);
   a.r[base + gc] = r;
   F[g.off + c] = (T)r;
@@ -150,7 +148,7 @@ __global__ void __launch_bounds__(256) k_aug(DevGeom G, GlobalLayout gl, LevelAr
   for (int k = 0; k < 11; ++k) acc[k] = 0.0;
   const int nx = gl.nx[lidx(L)], ny = gl.ny[lidx(L)], pitch = gl.pitch[lidx(L)];
   const int S = 1 << L;
-  const double h = level_h(G.H, L), m12 = h * h / 12.0, invS = 1.0 / S;
+  const double m12 = a.m12, invS = pow2(-L);
   const double* u = a.ut + (long long)p * gl.bstride;
   if (G.cell_in[cj * G.ncx + ci]) {
     for (int q = threadIdx.x; q < S * S; q += blockDim.x) {

@@ -61,6 +61,7 @@ struct LevelArgs {
   const double* c0;      // [B] coefficient of u~ in u_{h_k}
   const double* lam;     // [B][n+1] eigenvalue per level
   int lam_stride;        // n + 1
+  double m12;            // h_L^2 / 12, the weight of the consistent mass stencil on level L
 };
 void launch_interp(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, cudaStream_t s);
 void launch_rhs(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, cudaStream_t s);
