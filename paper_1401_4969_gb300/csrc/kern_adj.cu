@@ -204,14 +204,7 @@ __global__ void __launch_bounds__(256) k_rr_adj(DevGeom G, RRAdjArgs a) {
     cP[r] = cv;
   }
   __syncthreads();
-  auto band_mv_m = [&](const double* v, int r) {
-    double my = MH[(long long)r * bw1] * v[r];
-    for (int d = 1; d <= bw; ++d) {
-      if (r - d >= 0) my += MH[(long long)r * bw1 + d] * v[r - d];
-      if (r + d < N) my += MH[(long long)(r + d) * bw1 + d] * v[r + d];
-    }
-    return my;
-  };
+  auto band_mv_m = [&](const double* v, int r) { return coarse_band_mv(MH, bw, bw - 1, v, r, N); };
   // b = B c, s = c^T cbar
   {
     double v[2] = {0.0, 0.0};

@@ -137,6 +137,33 @@ __device__ inline void band_solve_shfl(const float* Ls, int ls, const float* inv
   __syncthreads();
 }
 
+// (A v)_q for a band of the T_H pencil (rows [q][d] = A(q, q - d), d = 0..bw, symmetric) in
+// grid-row order with b unknowns per row: the 5-point stiffness and the 7-point mass have
+// nonzeros only on the diagonals d = 0, 1, b, b + 1 (the W/E, S/N and SW/NE couplings), so
+// the product takes 7 terms instead of 2 bw + 1. The terms are added in the order of the
+// full band loop, so the result is the same bit for bit. b < 2 falls back to that loop.
+__device__ __forceinline__ double coarse_band_mv(const double* A, int bw, int b, const double* v, int q, int N) {
+  const long long bw1 = bw + 1;
+  double s = A[q * bw1] * v[q];
+  if (b < 2 || bw != b + 1) {
+    for (int d = 1; d <= bw; ++d) {
+      if (q - d >= 0) s += A[q * bw1 + d] * v[q - d];
+      if (q + d < N) s += A[(q + d) * bw1 + d] * v[q + d];
+    }
+    return s;
+  }
+  if (q >= 1) s += A[q * bw1 + 1] * v[q - 1];
+  if (q + 1 < N) s += A[(q + 1) * bw1 + 1] * v[q + 1];
+  if (q >= b) s += A[q * bw1 + b] * v[q - b];
+  if (q + b < N) s += A[(q + b) * bw1 + b] * v[q + b];
+  if (q >= b + 1) s += A[q * bw1 + b + 1] * v[q - b - 1];
+  if (q + b + 1 < N) s += A[(q + b + 1) * bw1 + b + 1] * v[q + b + 1];
+  return s;
+}
+
+// Diagonal slot k = 0..3 of the nonzero diagonals d = 0, 1, b, b + 1 of the T_H pencil band.
+__device__ __forceinline__ int coarse_band_diag(int k, int b) { return k < 2 ? k : b + (k - 2); }
+
 // Block LDL^T of the T_H pencil S = K_H - mu M_H by grid rows (FP32), for unknowns ordered
 // r = (Y-1) b + (X-1): S is block tridiagonal with b x b diagonal blocks S_II (couplings
 // W/E) and sub-diagonal blocks S_{I,I-1} holding only the S and SW couplings (row r: columns

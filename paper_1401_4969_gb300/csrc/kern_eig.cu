@@ -687,14 +687,7 @@ __global__ void __launch_bounds__(256) k_rr(DevGeom G, RRArgs a) {
   }
   __syncthreads();
 
-  auto band_mv_m = [&](const double* v, int r) {
-    double my = MH[(long long)r * bw1] * v[r];
-    for (int d = 1; d <= bw; ++d) {
-      if (r - d >= 0) my += MH[(long long)r * bw1 + d] * v[r - d];
-      if (r + d < N) my += MH[(long long)(r + d) * bw1 + d] * v[r + d];
-    }
-    return my;
-  };
+  auto band_mv_m = [&](const double* v, int r) { return coarse_band_mv(MH, bw, bw - 1, v, r, N); };
   // factor S(mu) and solve S y = w(mu); false if S(mu) is not positive definite
   auto factor_solve = [&](double mu) {
     for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) Lb[q] = KH[q] - mu * MH[q];
@@ -849,28 +842,25 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     MH = mh_s;
   }
   double smu = NAN;  // mu of the S band in sm_s (shared-memory mode)
-  // r_q = w_q - (S(mu) y)_q, from the staged S(mu) band when it is current
+  // r_q = w_q - (S(mu) y)_q, from the staged S(mu) band when it is current (only the
+  // diagonals d = 0, 1, b, b + 1 are nonzero: coarse_band_mv)
+  const int bb = bw - 1;
   auto resid_row = [&](const double* v, int q, double mu) {
-    if (a.smem && smu == mu) {
-      double s = sm_s[(long long)q * bw1] * v[q];
-      for (int d = 1; d <= bw; ++d) {
-        if (q - d >= 0) s += sm_s[(long long)q * bw1 + d] * v[q - d];
-        if (q + d < N) s += sm_s[(long long)(q + d) * bw1 + d] * v[q + d];
-      }
-      return wv[q] - s;
-    }
-    double sk = KH[(long long)q * bw1] * v[q], sm = MH[(long long)q * bw1] * v[q];
-    for (int d = 1; d <= bw; ++d) {
-      if (q - d >= 0) {
-        sk += KH[(long long)q * bw1 + d] * v[q - d];
-        sm += MH[(long long)q * bw1 + d] * v[q - d];
-      }
-      if (q + d < N) {
-        sk += KH[(long long)(q + d) * bw1 + d] * v[q + d];
-        sm += MH[(long long)(q + d) * bw1 + d] * v[q + d];
-      }
-    }
+    if (a.smem && smu == mu) return wv[q] - coarse_band_mv(sm_s, bw, bb, v, q, N);
+    const double sk = coarse_band_mv(KH, bw, bb, v, q, N), sm = coarse_band_mv(MH, bw, bb, v, q, N);
     return wv[q] - (sk - mu * sm);
+  };
+  // S(mu) into sm_s: the four nonzero diagonals (all that the products and the block factor read)
+  auto stage_s = [&](double mu) {
+    if (bb >= 2 && bw == bb + 1) {
+      for (int q = threadIdx.x; q < 4 * N; q += blockDim.x) {
+        const long long e = (long long)(q >> 2) * bw1 + coarse_band_diag(q & 3, bb);
+        sm_s[e] = kh_s[e] - mu * mh_s[e];
+      }
+    } else {
+      for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) sm_s[q] = kh_s[q] - mu * mh_s[q];
+    }
+    smu = mu;
   };
   const double* part = a.partials + (long long)p * ncx * ncy * 12;
   for (int q = threadIdx.x; q < npair; q += blockDim.x) {
@@ -903,14 +893,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     gb[q] = sb;
   }
   __syncthreads();
-  auto band_mv = [&](const double* M, const double* v, int q) {
-    double s = M[(long long)q * bw1] * v[q];
-    for (int d = 1; d <= bw; ++d) {
-      if (q - d >= 0) s += M[(long long)q * bw1 + d] * v[q - d];
-      if (q + d < N) s += M[(long long)(q + d) * bw1 + d] * v[q + d];
-    }
-    return s;
-  };
+  auto band_mv = [&](const double* M, const double* v, int q) { return coarse_band_mv(M, bw, bb, v, q, N); };
   double sig = NAN;  // shift of the current factors
   // FP32 factors of S(mu); false if S(mu) is not positive definite. Blocked mode: the block
   // LDL^T by grid rows (P_I^{-1} in Dinv, W_I in Loff) from the staged FP64 band S(mu);
@@ -918,10 +901,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   auto factor = [&](double mu) {
     sig = mu;
     if (a.blocked) {
-      if (smu != mu) {
-        for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) sm_s[q] = kh_s[q] - mu * mh_s[q];
-        smu = mu;
-      }
+      if (smu != mu) stage_s(mu);
       __syncthreads();
       return BS == 16 ? block_ldlt_f<16>(sm_s, bw1, bsz, nbk, Dinv, Loff, bwork, &bflag)
                       : block_ldlt_f<32>(sm_s, bw1, bsz, nbk, Dinv, Loff, bwork, &bflag);
@@ -951,10 +931,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   __syncthreads();
   auto start = [&](double mu) {
     for (int q = threadIdx.x; q < N; q += blockDim.x) wv[q] = ga[q] - mu * gb[q];
-    if (a.smem && smu != mu) {
-      for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) sm_s[q] = kh_s[q] - mu * mh_s[q];
-      smu = mu;
-    }
+    if (a.smem && smu != mu) stage_s(mu);
     __syncthreads();
     for (int q = threadIdx.x; q < N; q += blockDim.x) r[q] = resid_row(y, q, mu);
     __syncthreads();
