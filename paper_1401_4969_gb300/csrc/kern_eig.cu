@@ -389,7 +389,6 @@ template <typename T, int KK>
 __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, Level1Args a) {
   extern __shared__ __align__(16) unsigned char l1_raw[];
   __shared__ SmGrid<T> lv[kTailMaxLev];
-  __shared__ double scratch[16 * 4];
   __shared__ double red[4];
   __shared__ float gram[12];
   __shared__ float sh_coef[4];
@@ -438,7 +437,10 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
   const uint8_t* m0 = lv[0].m;
   const double h = level_h(G.H, 1), m12 = h * h / 12.0;
   const float m12f = (float)m12;
-#define L1_FOR_NODES for (int j = threadIdx.y; j <= ny; j += blockDim.y) for (int i = threadIdx.x; i <= nx; i += blockDim.x)
+// every node (i, j) of level 1 once, flat over the block (no half-empty warp passes)
+#define L1_FOR_NODES                                             \
+  for (int n_ = tid, j = n_ / W, i = n_ - j * W; n_ < nn;        \
+       n_ += nt, j = n_ / W, i = n_ - j * W)
   auto apply_km64 = [&]() {  // K x, M x in FP64
     L1_FOR_NODES {
       const int q = j * W + i;
@@ -463,33 +465,36 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
   bool have_p = false;
   int it = 0;
   double res = 1.0, rho = 0.0;
+  // FP64 sums staged in the Gram buffer (free outside the Gram step), flat node loops (the
+  // sums and the residual need no (i, j)); the stopping test compares squares
+  double* stage = reinterpret_cast<double*>(G11);
+  double r2 = 0.0, m2 = 1.0;
   for (; it < a.max_iter; ++it) {
     {  // FP64 Rayleigh quotient of x
       double v[2] = {0.0, 0.0};
-      L1_FOR_NODES {
-        const int q = j * W + i;
+      for (int q = tid; q < nn; q += nt) {
         v[0] += X[q] * KX[q];
         v[1] += X[q] * MX[q];
       }
-      block_sum_2d<2>(v, scratch, red);
+      block_sum_t<2>(v, stage, red);
       rho = red[0] / red[1];
     }
     {
       double v[2] = {0.0, 0.0};
-      L1_FOR_NODES {
-        const int q = j * W + i;
+      for (int q = tid; q < nn; q += nt) {
         const double r = KX[q] - rho * MX[q];
         R[q] = r;
         v[0] += r * r;
         v[1] += MX[q] * MX[q];
       }
-      block_sum_2d<2>(v, scratch, red);
-      res = sqrt(red[0]) / (rho * sqrt(red[1]));
+      block_sum_t<2>(v, stage, red);
+      r2 = red[0];
+      m2 = red[1];
     }
-    if (res < a.tol) break;
+    // relative eigen-residual |r| / (rho |M x|) < tol
+    if (r2 < a.tol * a.tol * rho * rho * m2) break;
     // preconditioner: one V-cycle for K w = r from w = 0, all grids on chip
-    L1_FOR_NODES {
-      const int q = j * W + i;
+    for (int q = tid; q < nn; q += nt) {
       lv[0].f[q] = m0[q] ? (T)R[q] : (T)0;
       lv[0].x[q] = (T)0;
     }
@@ -503,10 +508,7 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
       tail_prolong<T>(lv[d], lv[d + 1]);
       tail_smooth<T, KK>(G, lv[d], a.post, true, (T)a.omega);
     }
-    L1_FOR_NODES {
-      const int q = j * W + i;
-      Wv[q] = (float)lv[0].x[q];
-    }
+    for (int q = tid; q < nn; q += nt) Wv[q] = (float)lv[0].x[q];
     __syncthreads();
     // K w, M w in FP32 and the FP32 Gram sums
     {
@@ -568,8 +570,7 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
     // x <- ca x + cb w + cp p (FP64 accumulation); p <- s (cb w + cp p) with its images
     const double ca = sh_coef[0];
     const float cb = sh_coef[1], cp = sh_coef[2], sp = sh_coef[3];
-    L1_FOR_NODES {
-      const int q = j * W + i;
+    for (int q = tid; q < nn; q += nt) {
       const float pn = cb * Wv[q] + cp * P[q];
       X[q] = ca * X[q] + (double)pn;
       P[q] = sp * pn;
@@ -580,14 +581,14 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
     __syncthreads();
     apply_km64();
   }
+  res = sqrt(r2) / (rho * sqrt(m2));
   double v[3] = {0.0, 0.0, 0.0};
-  L1_FOR_NODES {
-    const int q = j * W + i;
+  for (int q = tid; q < nn; q += nt) {
     v[0] += X[q] * KX[q];
     v[1] += X[q] * MX[q];
     v[2] += X[q];
   }
-  block_sum_2d<3>(v, scratch, red);
+  block_sum_t<3>(v, stage, red);
   const double lam = red[0] / red[1];
   const double sc = (red[2] >= 0 ? 1.0 : -1.0) / sqrt(red[1]);
   double* out = a.ut1 + (long long)p * gl.bstride;

@@ -134,4 +134,26 @@ __device__ void block_sum_2d(double (&v)[NV], double* scratch, double* out) {
   __syncthreads();
 }
 
+// The same sums with few FP64 instructions (an FP64 add holds an SM sub-partition's FP64 pipe
+// for ~64 cycles, so a shuffle tree in every warp is throughput-bound): each thread stores
+// its NV values to `stage` ([NV][nt] doubles), then warp k alone adds quantity k (nt / 32
+// values per lane, then one shuffle tree). Needs NV <= number of warps. All threads call it;
+// `out` is valid after the return.
+template <int NV>
+__device__ void block_sum_t(const double (&v)[NV], double* stage, double* out) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) stage[k * nt + tid] = v[k];
+  __syncthreads();
+  if (warp < NV) {
+    double a = 0.0;
+    for (int q = lane; q < nt; q += 32) a += stage[warp * nt + q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) out[warp] = a;
+  }
+  __syncthreads();
+}
+
 }  // namespace mlev
