@@ -169,21 +169,24 @@ __device__ __forceinline__ int coarse_band_diag(int k, int b) { return k < 2 ? k
 // W/E) and sub-diagonal blocks S_{I,I-1} holding only the S and SW couplings (row r: columns
 // r and r - 1). With W_I = S_{I,I-1} P_{I-1}^{-1} and P_I = S_II - W_I S_{I,I-1}^T
 // (P_0 = S_00), S = L P L^T with L unit block lower bidiagonal (L_{I,I-1} = W_I) and P block
-// diagonal; the blocks are stored as BS x BS tiles (zero padded) with row stride BS + 1
-// (blk_ld), so that a warp reading one row per lane or one column per lane hits 32
-// different shared-memory banks: Pinv[I] = P_I^{-1} and W[I]. Sparse S_{I,I-1} makes W_I
-// and P_I O(b^2) each; P_I is inverted by warp 0 alone (Gauss-Jordan with warp shuffles;
-// for BS = 16 lanes 0-15 reduce the rows of P_I and lanes 16-31 carry the rows of the
-// inverse). The band S(mu) (FP64, [r][d] = S(r, r-d)) is read from shared memory. `work`
-// holds 2 tiles. Returns false (to all threads) if a pivot is not positive (S(mu) not
-// positive definite); `flag` is a shared int.
+// diagonal; the blocks are stored as BS x BS tiles (zero padded) with row stride BS + 4
+// (blk_ld): rows start on 16-byte boundaries, so the solve reads a row as float4 vectors,
+// and a quarter-warp reading 8 rows as float4 (or a warp reading one column per lane) hits
+// distinct shared-memory banks. Pinv[I] = P_I^{-1}, W[I] and its transpose WT[I] (the
+// backward sweep reads W_{I+1}^T by rows). Sparse S_{I,I-1} makes W_I and P_I O(b^2) each;
+// P_I is inverted by warp 0 alone (Gauss-Jordan with warp shuffles; for BS = 16 lanes 0-15
+// reduce the rows of P_I and lanes 16-31 carry the rows of the inverse). The band S(mu)
+// (FP64, [r][d] = S(r, r-d)) is read from shared memory. `work` holds 2 tiles. Returns false
+// (to all threads) if a pivot is not positive (S(mu) not positive definite); `flag` is a
+// shared int. All tile pointers 16-byte aligned.
 template <int BS>
-__host__ __device__ constexpr int blk_ld() { return BS + 1; }
+__host__ __device__ constexpr int blk_ld() { return BS + 4; }
 template <int BS>
-__host__ __device__ constexpr int blk_tile() { return BS * (BS + 1); }
+__host__ __device__ constexpr int blk_tile() { return BS * (BS + 4); }
 
 template <int BS>
-__device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pinv, float* W, float* work, int* flag) {
+__device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pinv, float* W, float* WT, float* work,
+                             int* flag) {
   constexpr int T2 = BS * BS, LD = blk_ld<BS>(), TS = blk_tile<BS>();
   const int tid = threadIdx.x, nt = blockDim.x;
   float* A = work;        // P_I before inversion
@@ -195,6 +198,7 @@ __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pi
   for (int I = 0; I < nb; ++I) {
     const float* Pp = Pinv + (long long)(I - 1) * TS;
     float* Wi = W + (long long)I * TS;
+    float* WTi = WT + (long long)I * TS;
     // S_{I,I-1} (two nonzeros per row) and W_I = S_{I,I-1} P_{I-1}^{-1}
     if (I > 0) {
       for (int q = tid; q < T2; q += nt) {
@@ -211,11 +215,13 @@ __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pi
         const int r = q / BS, c = q % BS;
         float v = Sub[r * LD + r] * Pp[r * LD + c];
         if (r > 0) v += Sub[r * LD + r - 1] * Pp[(r - 1) * LD + c];
-        Wi[r * LD + c] = (r < b && c < b) ? v : 0.f;
+        v = (r < b && c < b) ? v : 0.f;
+        Wi[r * LD + c] = v;
+        WTi[c * LD + r] = v;
       }
       __syncthreads();
     } else {
-      for (int q = tid; q < T2; q += nt) Wi[(q / BS) * LD + q % BS] = 0.f;
+      for (int q = tid; q < T2; q += nt) Wi[(q / BS) * LD + q % BS] = WTi[(q / BS) * LD + q % BS] = 0.f;
     }
     // P_I = S_II - W_I S_{I,I-1}^T  ((S^T)_{kc} nonzero for k = c, c - 1... i.e. Sub[c][k], k in {c, c-1})
     for (int q = tid; q < T2; q += nt) {
@@ -294,58 +300,48 @@ __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pi
   return true;
 }
 
-// S x = y in place with the block factors (L_{I,I-1} = W_I, P_I^{-1}): forward
-// u_I = y_I - W_I u_{I-1} (in place), backward x_I = P_I^{-1} u_I - W_{I+1}^T x_{I+1}, by
-// warp 0 (lane = row; rows and columns of the padded tiles are conflict-free). y must be
-// followed by BS readable finite floats; t is BS floats of scratch.
+// S x = y with the block factors (L_{I,I-1} = W_I, P_I^{-1}): forward
+// u_I = y_I - W_I u_{I-1} in place in yp, backward x_I = P_I^{-1} u_I - W_{I+1}^T x_{I+1} into
+// xp, by warp 0 (lane = row). yp and xp hold block I at [I * BS, I * BS + b) with the BS - b
+// padding entries zero, 16-byte aligned; every row product is BS / 4 float4 loads of the
+// tile row and BS / 4 broadcast float4 loads of the vector.
 template <int BS>
-__device__ inline void block_solve_f(const float* Pinv, const float* W, float* y, float* t, int b, int nb) {
+__device__ __forceinline__ float blk_dot(const float* row, const float* v) {
+  const float4* a4 = reinterpret_cast<const float4*>(row);
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+  for (int k = 0; k < BS / 4; ++k) {
+    const float4 x = a4[k], y = v4[k];
+    s0 = fmaf(x.x, y.x, s0);
+    s1 = fmaf(x.y, y.y, s1);
+    s2 = fmaf(x.z, y.z, s2);
+    s3 = fmaf(x.w, y.w, s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+template <int BS>
+__device__ inline void block_solve_f(const float* Pinv, const float* W, const float* WT, float* yp, float* xp, int b,
+                                     int nb) {
   if (threadIdx.x < 32) {
     constexpr int LD = blk_ld<BS>(), TS = blk_tile<BS>();
     const int r = threadIdx.x;
     for (int I = 1; I < nb; ++I) {
-      if (r < b) {
-        const float* Wr = W + (long long)I * TS + r * LD;
-        const float* up = y + (I - 1) * b;
-        float s0 = y[I * b + r], s1 = 0.f;
-#pragma unroll
-        for (int c = 0; c < BS; c += 2) {
-          s0 -= Wr[c] * up[c];
-          s1 -= Wr[c + 1] * up[c + 1];
-        }
-        y[I * b + r] = s0 + s1;  // lane r alone reads and writes entry r of block I
-      }
+      if (r < b) yp[I * BS + r] -= blk_dot<BS>(W + (long long)I * TS + r * LD, yp + (I - 1) * BS);
       __syncwarp();
     }
     for (int I = nb - 1; I >= 0; --I) {
       if (r < b) {
-        const float* Pr = Pinv + (long long)I * TS + r * LD;
-        const float* u = y + I * b;
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int c = 0; c < BS; c += 2) {
-          s0 += Pr[c] * u[c];
-          s1 += Pr[c + 1] * u[c + 1];
-        }
-        if (I + 1 < nb) {
-          const float* Wn = W + (long long)(I + 1) * TS;  // column r of W_{I+1}
-          const float* xn = y + (I + 1) * b;
-#pragma unroll
-          for (int c = 0; c < BS; c += 2) {
-            s0 -= Wn[c * LD + r] * xn[c];
-            s1 -= Wn[(c + 1) * LD + r] * xn[c + 1];
-          }
-        }
-        t[r] = s0 + s1;
+        float v = blk_dot<BS>(Pinv + (long long)I * TS + r * LD, yp + I * BS);
+        if (I + 1 < nb) v -= blk_dot<BS>(WT + (long long)(I + 1) * TS + r * LD, xp + (I + 1) * BS);
+        xp[I * BS + r] = v;
       }
-      __syncwarp();
-      if (r < b) y[I * b + r] = t[r];
       __syncwarp();
     }
   }
   __syncthreads();
 }
-
 
 // Factors of S(sigma) = K_H - sigma M_H for the Rayleigh-Ritz step of level L, prepared by
 // one block of the inner-product kernel of the same level (which runs just before the
@@ -373,17 +369,18 @@ __device__ inline void rr_prefactor_block(const double* KH, const double* MH, co
     if (threadIdx.x == 0) *reinterpret_cast<int*>(out + 8) = 0;
     return;
   }
-  const int BS = bsz <= 16 ? 16 : 32, TS = BS * (BS + 1);
-  double* sb = sm;                                                   // S(sigma), FP64 band
-  float* tiles = reinterpret_cast<float*>(sb + (long long)N * bw1);  // P_I^{-1} tiles, then W_I
-  float* work = tiles + 2LL * nbk * TS;
+  const int BS = bsz <= 16 ? 16 : 32, TS = BS * (BS + 4);
+  double* sb = sm;  // S(sigma), FP64 band; then P_I^{-1}, W_I and W_I^T tiles (16-byte aligned)
+  float* tiles = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sb + (long long)N * bw1) + 15) & ~uintptr_t(15));
+  float* work = tiles + 3LL * nbk * TS;
   for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) sb[q] = KH[q] - sigma * MH[q];
   __syncthreads();
-  const bool ok = BS == 16 ? block_ldlt_f<16>(sb, bw1, bsz, nbk, tiles, tiles + (long long)nbk * TS, work, flag)
-                           : block_ldlt_f<32>(sb, bw1, bsz, nbk, tiles, tiles + (long long)nbk * TS, work, flag);
+  float* W = tiles + (long long)nbk * TS;
+  const bool ok = BS == 16 ? block_ldlt_f<16>(sb, bw1, bsz, nbk, tiles, W, W + (long long)nbk * TS, work, flag)
+                           : block_ldlt_f<32>(sb, bw1, bsz, nbk, tiles, W, W + (long long)nbk * TS, work, flag);
   float* dst = reinterpret_cast<float*>(out + 16);
   if (ok)
-    for (long long q = threadIdx.x; q < 2LL * nbk * TS; q += blockDim.x) dst[q] = tiles[q];
+    for (long long q = threadIdx.x; q < 3LL * nbk * TS; q += blockDim.x) dst[q] = tiles[q];
   if (threadIdx.x == 0) {
     *reinterpret_cast<double*>(out) = sigma;
     *reinterpret_cast<int*>(out + 8) = ok ? 1 : 0;

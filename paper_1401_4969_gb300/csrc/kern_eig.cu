@@ -821,16 +821,20 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   float* r32 = invD + N;                                    // N + 32 entries, the tail kept at 0
   const int bsz = bw - 1, nbk = bsz > 0 ? N / bsz : 0;     // row blocks (blocked solves)
   const int BS = bsz <= 16 ? 16 : 32;                      // padded tile edge
-  const int TS = BS * (BS + 1);                            // tile with row stride BS + 1
-  float* Dinv = r32 + N + 32;
-  float* Loff = Dinv + (a.blocked ? (long long)nbk * TS : 0);
-  float* tb = Loff + (a.blocked ? (long long)nbk * TS : 0);
-  float* bwork = tb + (a.blocked ? BS : 0);                // 2 tiles (block factorisation)
+  const int TS = BS * (BS + 4);                            // tile with row stride BS + 4
+  // blocked mode (16-byte aligned): P_I^{-1}, W_I, W_I^T tiles, the padded right-hand side
+  // yp and solution xp (block I at I * BS), 2 work tiles
+  float* Dinv = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(r32 + N + 32) + 15) & ~uintptr_t(15));
+  const long long tiles = a.blocked ? (long long)nbk * TS : 0, vecs = a.blocked ? (long long)nbk * BS : 0;
+  float* Loff = Dinv + tiles;
+  float* LT = Loff + tiles;
+  float* yp = LT + tiles;
+  float* xp = yp + vecs;
+  float* bwork = xp + vecs;
   int* pairs = reinterpret_cast<int*>(a.smem ? bwork + (a.blocked ? 2 * TS : 0) : reinterpret_cast<float*>(rr_sm));
   if (a.smem) {
     for (int q = threadIdx.x; q < 32; q += blockDim.x) r32[N + q] = 0.f;
-    if (a.blocked)
-      for (int q = threadIdx.x; q < BS; q += blockDim.x) tb[q] = 0.f;
+    for (long long q = threadIdx.x; q < 2 * vecs; q += blockDim.x) yp[q] = 0.f;  // padding stays 0
   }
   const double* KH = a.KH + (long long)p * N * bw1;
   const double* MH = a.MH + (long long)p * N * bw1;
@@ -904,8 +908,8 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     if (a.blocked) {
       if (smu != mu) stage_s(mu);
       __syncthreads();
-      return BS == 16 ? block_ldlt_f<16>(sm_s, bw1, bsz, nbk, Dinv, Loff, bwork, &bflag)
-                      : block_ldlt_f<32>(sm_s, bw1, bsz, nbk, Dinv, Loff, bwork, &bflag);
+      return BS == 16 ? block_ldlt_f<16>(sm_s, bw1, bsz, nbk, Dinv, Loff, LT, bwork, &bflag)
+                      : block_ldlt_f<32>(sm_s, bw1, bsz, nbk, Dinv, Loff, LT, bwork, &bflag);
     }
     for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) Lb[q] = (float)(KH[q] - mu * MH[q]);
     if (!band_ldlt_f(Lb, invD, pairs, npair, N, bw)) return false;
@@ -939,15 +943,20 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   };
   // y += S(sigma)^{-1} r (FP32 factors), then r = w - S(mu) y in FP64; returns |r|^2 / |w|^2
   auto refine = [&](double mu) {
-    for (int q = threadIdx.x; q < N; q += blockDim.x) r32[q] = (float)r[q];
-    __syncthreads();
-    if (a.blocked && BS == 16)
-      block_solve_f<16>(Dinv, Loff, r32, tb, bsz, nbk);
-    else if (a.blocked)
-      block_solve_f<32>(Dinv, Loff, r32, tb, bsz, nbk);
-    else
+    if (a.blocked) {
+      for (int q = threadIdx.x; q < N; q += blockDim.x) yp[(q / bsz) * BS + q % bsz] = (float)r[q];
+      __syncthreads();
+      if (BS == 16)
+        block_solve_f<16>(Dinv, Loff, LT, yp, xp, bsz, nbk);
+      else
+        block_solve_f<32>(Dinv, Loff, LT, yp, xp, bsz, nbk);
+      for (int q = threadIdx.x; q < N; q += blockDim.x) y[q] += (double)xp[(q / bsz) * BS + q % bsz];
+    } else {
+      for (int q = threadIdx.x; q < N; q += blockDim.x) r32[q] = (float)r[q];
+      __syncthreads();
       band_solve_shfl(Lb, bw1, invD, r32, N, bw);
-    for (int q = threadIdx.x; q < N; q += blockDim.x) y[q] += (double)r32[q];
+      for (int q = threadIdx.x; q < N; q += blockDim.x) y[q] += (double)r32[q];
+    }
     __syncthreads();
     double v[2] = {0.0, 0.0};
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
@@ -994,7 +1003,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     const unsigned char* pp = a.pre + (long long)p * a.pre_stride;
     if (*reinterpret_cast<const int*>(pp + 8)) {
       const float* src = reinterpret_cast<const float*>(pp + 16);
-      for (long long q = threadIdx.x; q < 2LL * nbk * TS; q += blockDim.x) Dinv[q] = src[q];
+      for (long long q = threadIdx.x; q < 3 * tiles; q += blockDim.x) Dinv[q] = src[q];
       sig = *reinterpret_cast<const double*>(pp);
       factored = true;
     }
@@ -1079,15 +1088,16 @@ size_t rr_prefactor_smem(int nhb, int bw) {
   const int bsz = bw - 1;
   if (bsz <= 0 || bsz > 32) return (size_t)-1;
   const size_t bs = bsz <= 16 ? 16 : 32;
-  return (size_t)nhb * (bw + 1) * 8 + (2 * (size_t)(nhb / bsz) + 2) * bs * (bs + 1) * 4;
+  return (size_t)nhb * (bw + 1) * 8 + 16 + (3 * (size_t)(nhb / bsz) + 2) * bs * (bs + 4) * 4;
 }
 
 // Shared memory of k_rr_mixed: 5 FP64 vectors, K_H, M_H and S(mu), the FP32 band, 2 FP32
 // vectors, the row-blocked factors (blocked mode) and the pair table.
 size_t rr_mixed_smem_bytes(int nhb, int bw, int blocked) {
   const size_t bsz = bw - 1, bs = bsz <= 16 ? 16 : 32;
-  const size_t ts = bs * (bs + 1);  // padded tile
-  const size_t blk = blocked && bsz > 0 ? 2 * (nhb / bsz) * ts + bs + 2 * ts : 0;
+  const size_t ts = bs * (bs + 4);  // padded tile
+  // 3 tile sets, yp and xp, 2 work tiles, 4 floats of alignment slack
+  const size_t blk = blocked && bsz > 0 ? 3 * (nhb / bsz) * ts + 2 * (nhb / bsz) * bs + 2 * ts + 4 : 0;
   return (size_t)nhb * 5 * 8 + 3 * (size_t)nhb * (bw + 1) * 8 +
          ((size_t)nhb * (bw + 1) + 2 * (size_t)nhb + 32 + blk + 2) * 4 + (size_t)(bw * (bw + 1) / 2) * 4 + 16;
 }

@@ -102,11 +102,12 @@ static inline int mlev_stat_stride(int n) { return 4 + 3 * (n + 1); }
 
 /* Bytes per batch member of the Rayleigh-Ritz factors prepared ahead of a level (mixed
    precision, row-blocked factors): the shift sigma (double), a flag (int, 1 = valid), padding
-   to 16 bytes, then P_I^{-1} and W_I as BS x (BS + 1) float tiles for the nhb / (bw - 1) grid
-   rows (BS = 16 or 32). 0 when the coarse system has no row-blocked form. */
+   to 16 bytes, then P_I^{-1}, W_I and W_I^T as BS x (BS + 4) float tiles for the
+   nhb / (bw - 1) grid rows (BS = 16 or 32). 0 when the coarse system has no row-blocked
+   form. */
 static inline size_t mlev_rr_prefactor_stride(int nhb, int bw) {
   const int bsz = bw - 1;
   if (bsz <= 0 || bsz > 32 || nhb <= 0) return 0;
-  const size_t bs = bsz <= 16 ? 16 : 32, ts = bs * (bs + 1);
-  return 16 + ((2 * (size_t)(nhb / bsz) * ts * 4 + 15) / 16) * 16;
+  const size_t bs = bsz <= 16 ? 16 : 32, ts = bs * (bs + 4);
+  return 16 + ((3 * (size_t)(nhb / bsz) * ts * 4 + 15) / 16) * 16;
 }

@@ -58,8 +58,13 @@ CASES = {
     "single-subdomain": lambda: W.single_subdomain(4, 3),
     "two-levels": lambda: W.config1().with_levels(2),
     "overlap2-delta-quarter": lambda: W.unit_square(6, 3, 3, overlap=2, delta_in_H=0.25),
-    # 19 coarse unknowns per grid row: the mixed Rayleigh-Ritz factor uses 32-wide row blocks
+    # 19 coarse unknowns per grid row (too large for the on-chip blocked factor: band path)
     "coarse-20x20": lambda: W.unit_square(20, 4, 3),
+    # 19 unknowns per grid row, 5 rows: the mixed Rayleigh-Ritz factor uses 32-wide row blocks
+    "rect-20x6": lambda: W.Problem(
+        name="rect20x6", ncx=20, ncy=6, x0=0.0, y0=0.0, H=0.05, cell_in=np.ones((6, 20), np.uint8),
+        cell_owner=np.array([[c // 5 for c in range(20)]] * 6, np.int32),
+        overlap=np.ones(4, np.int32), delta=0.025, levels=3),
     "ragged-6x4": lambda: W.Problem(
         name="rect6x4", ncx=6, ncy=4, x0=0.0, y0=0.0, H=0.25, cell_in=np.ones((4, 6), np.uint8),
         cell_owner=np.array([[0, 0, 0, 1, 1, 1]] * 2 + [[2, 2, 2, 3, 3, 3]] * 2, np.int32),
