@@ -473,9 +473,11 @@ struct Launcher {
       // memory, still runs in one wave (a batch of many problems would lose occupancy there)
       const size_t pre_smem = rr_prefactor_smem(P.nhb, P.bw);
       const long long aug_blocks = (long long)B * (P.ncx * P.ncy + 1);
-      const long long aug_slots = (long long)ctx->sm_count * (long long)(ctx->smem_per_sm / (pre_smem + 1024));
-      rr.use_pre = rr.blocked && rr.smem && L >= 4 && P.w_rrpre.bytes > 0 && pre_smem <= (size_t)kRRSmemMax &&
-                           aug_blocks <= aug_slots ? 1 : 0;
+      // (per block: the factor's dynamic memory, the kernel's 22.6 KB of static staging and the
+      // 1 KB the runtime reserves)
+      const long long aug_slots = (long long)ctx->sm_count * (long long)(ctx->smem_per_sm / (pre_smem + 24 * 1024));
+      rr.use_pre = rr.blocked && rr.smem && L >= 4 && P.bw - 1 <= 16 && P.w_rrpre.bytes > 0 &&
+                           pre_smem <= (size_t)kRRSmemMax && aug_blocks <= aug_slots ? 1 : 0;
       const RRPrefactor pf{KH, MH, P.nhb, P.bw, rr.pre, rr.pre_stride};
       go(F_INTERP, 10.0 * nfree, [&] { launch_interp(G, P.glay, a, s); });
       go(F_RHS, (16.0 + kfine_extra()) * nfree, [&] { launch_rhs(G, P.glay, a, s); });

@@ -352,12 +352,14 @@ __device__ inline void block_solve_f(const float* Pinv, const float* W, const fl
 // and corner-limited rates) is used; the Rayleigh-Ritz kernel refines against these
 // factors and refactors at its own mu if the refinement stalls. `out` holds the layout of
 // mlev_rr_prefactor_stride; `sm` is dynamic shared memory of rr_prefactor_smem bytes.
-// Called by all threads of the block.
+// Called by all threads of the block. Only for 16-wide row blocks (b <= 16): the 32-wide
+// Gauss-Jordan would raise the register count of every block of the host kernel.
 __device__ inline void rr_prefactor_block(const double* KH, const double* MH, const double* lamp, int L, int nhb,
                                           int bw, unsigned char* out, double* sm, int* flag) {
+  constexpr int BS = 16, TS = BS * (BS + 4);
   const int N = nhb, bw1 = bw + 1, bsz = bw - 1, nbk = N / bsz;
   double sigma = NAN;
-  bool use = L >= 4;
+  bool use = L >= 4 && bsz <= BS;
   if (use) {
     const double l1 = lamp[L - 1], l2 = lamp[L - 2], l3 = lamp[L - 3];
     const double d1 = l2 - l1, d2 = l3 - l2;
@@ -369,15 +371,13 @@ __device__ inline void rr_prefactor_block(const double* KH, const double* MH, co
     if (threadIdx.x == 0) *reinterpret_cast<int*>(out + 8) = 0;
     return;
   }
-  const int BS = bsz <= 16 ? 16 : 32, TS = BS * (BS + 4);
   double* sb = sm;  // S(sigma), FP64 band; then P_I^{-1}, W_I and W_I^T tiles (16-byte aligned)
   float* tiles = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sb + (long long)N * bw1) + 15) & ~uintptr_t(15));
   float* work = tiles + 3LL * nbk * TS;
   for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) sb[q] = KH[q] - sigma * MH[q];
   __syncthreads();
   float* W = tiles + (long long)nbk * TS;
-  const bool ok = BS == 16 ? block_ldlt_f<16>(sb, bw1, bsz, nbk, tiles, W, W + (long long)nbk * TS, work, flag)
-                           : block_ldlt_f<32>(sb, bw1, bsz, nbk, tiles, W, W + (long long)nbk * TS, work, flag);
+  const bool ok = block_ldlt_f<BS>(sb, bw1, bsz, nbk, tiles, W, W + (long long)nbk * TS, work, flag);
   float* dst = reinterpret_cast<float*>(out + 16);
   if (ok)
     for (long long q = threadIdx.x; q < 3LL * nbk * TS; q += blockDim.x) dst[q] = tiles[q];

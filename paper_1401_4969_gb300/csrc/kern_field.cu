@@ -5,6 +5,7 @@
 #include "kern_band.cuh"
 #include "kern_coarse.cuh"
 #include "kern_launch.h"
+#include "kern_tail.cuh"
 
 namespace mlev {
 
@@ -126,7 +127,7 @@ template <int KK, bool PRE>
 __global__ void __launch_bounds__(256) k_aug(DevGeom G, GlobalLayout gl, LevelArgs a, double* partials,
                                              RRPrefactor pf) {
   extern __shared__ double aug_dyn[];
-  __shared__ double scratch[8 * 11];
+  __shared__ double stage[11 * 256];
   __shared__ double outv[11];
   __shared__ int pflag;
   // with PRE, blocks [0, B) prepare the Rayleigh-Ritz factors (first, so they start first),
@@ -148,33 +149,58 @@ __global__ void __launch_bounds__(256) k_aug(DevGeom G, GlobalLayout gl, LevelAr
   for (int k = 0; k < 11; ++k) acc[k] = 0.0;
   const int nx = gl.nx[lidx(L)], ny = gl.ny[lidx(L)], pitch = gl.pitch[lidx(L)];
   const int S = 1 << L;
-  const double m12 = a.m12, invS = pow2(-L);
+  const double invS = pow2(-L);
   const double* u = a.ut + (long long)p * gl.bstride;
   if (G.cell_in[cj * G.ncx + ci]) {
-    for (int q = threadIdx.x; q < S * S; q += blockDim.x) {
-      const int ri = q & (S - 1), rj = q >> L;
-      const int i = (ci << L) + ri, j = (cj << L) + rj;
-      if (!is_free(G, L, nx, ny, i, j)) continue;
-      const long long c = (long long)j * pitch + i;
-      const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
-      const double uc = u[c];
-      const double ku = apply_k<double, double>(u, c, pitch, w);
-      const double mu = m12 * apply_m12<double, double>(u, c, pitch);
-      acc[0] += uc * ku;
-      acc[1] += uc * mu;
-      acc[2] += uc;
-      const double s = ri * invS, t = rj * invS;
-      double p00, p10, p01, p11;
-      if (ri >= rj) {
-        p00 = 1.0 - s; p10 = s - t; p01 = 0.0; p11 = t;
-      } else {
-        p00 = 1.0 - t; p10 = 0.0; p01 = t - s; p11 = s;
+    // Thread layout: a fixed column ri of the cell (s = ri / S) and every nt/S-th row. The
+    // hats of the cell's corners are linear in t = rj / S on each triangle (lower rj <= ri:
+    // 1 - s, s - t, 0, t; upper: 1 - t, 0, t - s, s), so per thread and column it suffices
+    // to sum ku, t ku, mu, t mu over the lower and the upper nodes; the weights are applied
+    // once per column and h^2 / 12 once at the end.
+    const int nt = blockDim.x;
+    const int cstep = S < nt ? S : nt, rstep = S < nt ? nt / S : 1;
+    for (int ri = threadIdx.x % cstep; ri < S; ri += cstep) {
+      const double s = ri * invS, dt = rstep * invS;
+      double skl = 0.0, tkl = 0.0, sml = 0.0, tml = 0.0, sku = 0.0, tku = 0.0, smu = 0.0, tmu = 0.0;
+      int rj = S < nt ? threadIdx.x / S : 0;
+      double t = rj * invS;
+      for (; rj < S; rj += rstep, t += dt) {
+        const int i = (ci << L) + ri, j = (cj << L) + rj;
+        if (!is_free(G, L, nx, ny, i, j)) continue;
+        const long long c = (long long)j * pitch + i;
+        const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
+        const double uc = u[c];
+        const double ku = apply_k<double, double>(u, c, pitch, w);
+        const double mu = apply_m12<double, double>(u, c, pitch);  // M u / (h^2 / 12)
+        acc[0] += uc * ku;
+        acc[1] += uc * mu;
+        acc[2] += uc;
+        if (rj > ri) {  // upper triangle
+          sku += ku;
+          tku += t * ku;
+          smu += mu;
+          tmu += t * mu;
+        } else {
+          skl += ku;
+          tkl += t * ku;
+          sml += mu;
+          tml += t * mu;
+        }
       }
-      acc[3] += p00 * ku; acc[4] += p10 * ku; acc[5] += p01 * ku; acc[6] += p11 * ku;
-      acc[7] += p00 * mu; acc[8] += p10 * mu; acc[9] += p01 * mu; acc[10] += p11 * mu;
+      acc[3] += (1.0 - s) * skl + sku - tku;
+      acc[4] += s * skl - tkl;
+      acc[5] += tku - s * sku;
+      acc[6] += tkl + s * sku;
+      acc[7] += (1.0 - s) * sml + smu - tmu;
+      acc[8] += s * sml - tml;
+      acc[9] += tmu - s * smu;
+      acc[10] += tml + s * smu;
     }
+    acc[1] *= a.m12;
+#pragma unroll
+    for (int k = 7; k < 11; ++k) acc[k] *= a.m12;
   }
-  block_sum<11>(acc, scratch, outv);
+  block_sum_t<11>(acc, stage, outv);
   if (threadIdx.x < 11) partials[((long long)p * G.ncx * G.ncy + cj * G.ncx + ci) * 12 + threadIdx.x] = outv[threadIdx.x];
 }
 

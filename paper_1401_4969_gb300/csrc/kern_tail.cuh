@@ -136,22 +136,22 @@ __device__ void block_sum_2d(double (&v)[NV], double* scratch, double* out) {
 
 // The same sums with few FP64 instructions (an FP64 add holds an SM sub-partition's FP64 pipe
 // for ~64 cycles, so a shuffle tree in every warp is throughput-bound): each thread stores
-// its NV values to `stage` ([NV][nt] doubles), then warp k alone adds quantity k (nt / 32
-// values per lane, then one shuffle tree). Needs NV <= number of warps. All threads call it;
-// `out` is valid after the return.
+// its NV values to `stage` ([NV][nt] doubles), then warp w adds quantities w, w + nwarps, ...
+// (nt / 32 values per lane, then one shuffle tree). All threads call it; `out` is valid after
+// the return.
 template <int NV>
 __device__ void block_sum_t(const double (&v)[NV], double* stage, double* out) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
-  const int lane = tid & 31, warp = tid >> 5;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
 #pragma unroll
   for (int k = 0; k < NV; ++k) stage[k * nt + tid] = v[k];
   __syncthreads();
-  if (warp < NV) {
+  for (int k = warp; k < NV; k += nw) {
     double a = 0.0;
-    for (int q = lane; q < nt; q += 32) a += stage[warp * nt + q];
+    for (int q = lane; q < nt; q += 32) a += stage[k * nt + q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    if (lane == 0) out[warp] = a;
+    if (lane == 0) out[k] = a;
   }
   __syncthreads();
 }
