@@ -33,10 +33,16 @@ REL_TOL = 1e-8
 
 
 # Schedules (cycle and sweep counts) come from the autotuner: the fastest schedule whose
-# eigenvalue stays within 0.1 x the 1e-8 bar of a conservative FP64 GPU solve, tuned
+# eigenvalue stays within 0.25 x the 1e-8 bar of a conservative FP64 GPU solve, tuned
 # separately for the mixed path and for the plain FP64 comparator (equal accuracy target).
 # The timed result is then checked against the stored oracle eigenvalue.
 TUNED = {"mixed": None, "fp64": None}
+
+
+def autotune_safety():
+    from paper_1401_4969_gb300 import autotune
+
+    return autotune.SAFETY
 
 
 def mixed_opts(mlev, graph=1):
@@ -379,7 +385,7 @@ def main():
                    "flush": "L2 flushed (512 MB write) before every timed step",
                    "opts": dict(TUNED["mixed"].opts),
                    "opts_fp64": None if TUNED["fp64"] is None else dict(TUNED["fp64"].opts),
-                   "autotune": {"target_rel": REL_TOL, "safety": 0.1,
+                   "autotune": {"target_rel": REL_TOL, "safety": autotune_safety(),
                                 "reference": "FP64 GPU solve, 6 V-cycles x 2 passes",
                                 "mixed_trials": len(TUNED["mixed"].trials),
                                 "mixed_err_vs_reference": TUNED["mixed"].err,

@@ -18,9 +18,10 @@ def _model(o):
 
 def test_search_picks_the_fastest_schedule_within_target():
     res = AT.search(_model, target_rel=1e-8)
-    assert all(t.err <= 1e-9 for t in res.trials if t.ok)
+    bar = AT.SAFETY * 1e-8
+    assert all(t.err <= bar for t in res.trials if t.ok)
     ms, err = _model({**res.opts})
-    assert err <= 1e-9
+    assert err <= bar
     # no accepted trial is faster than the result
     assert min(t.ms for t in res.trials if t.ok) == pytest.approx(res.ms)
     assert res.opts["fused"] == 1 and res.opts["coarse_sweeps"] == 10
