@@ -282,7 +282,7 @@ struct Launcher {
   template <typename T>
   void solve_set(const std::vector<TileList>& lists, const TileList& coarsest, int vcycles, T* X, T* F, double* X64,
                  const double* R, int cmode, const std::vector<TileList>* fl = nullptr, int dt = 0,
-                 const TileList* tail = nullptr, size_t tail_smem = 0, bool rmask = false) {
+                 const TileList* tail = nullptr, size_t tail_smem = 0, bool rmask = false, bool accum_out = true) {
     const int D = (int)lists.size() - 1;
     const bool fused = o.fused == 1 && fl && tail && dt <= D && o.pre_smooth >= 1 && o.pre_smooth <= 2 &&
                        o.post_smooth >= 1 && o.post_smooth <= 2;
@@ -311,7 +311,7 @@ struct Launcher {
           vcycle<T>(lists, coarsest, X, F, cmode);
       }
     }
-    if (mixed)
+    if (mixed && accum_out)
       go(F_ACCUM, (2 * t + 16) * top.unk, [&] { launch_accumulate<T>(G, tiles_at(top), top.count, X, X64, s); });
   }
 
@@ -488,8 +488,12 @@ struct Launcher {
       const TileList& top = lp.sub[0];
       go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * top.unk,
          [&] { launch_gather<T>(G, P.glay, tiles_at(top), top.count, X, F, X64, r, s); });
+      // with one pass the FP64 accumulator would only be the FP32 solution widened: glue and
+      // the strip update read the FP32 pool directly (same values) unless residuals are checked
+      const bool direct32 = mixed && o.refine_passes == 1 && !o.check_residuals;
+      const float* E32 = direct32 ? reinterpret_cast<const float*>(X) : nullptr;
       solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, r, sub_cmode, &lp.sub_f, lp.sub_dt, &lp.sub_tail,
-                   lp.sub_tail_smem);
+                   lp.sub_tail_smem, false, !direct32);
       const double* E = mixed ? X64 : reinterpret_cast<const double*>(X);
       if (o.check_residuals) {
         cudaMemsetAsync(jobnorm, 0, P.w_jobnorm.bytes, s);
@@ -499,13 +503,13 @@ struct Launcher {
            [&] { launch_resnorm_finalize(jobnorm, B, P.m, 1, stat, stat_stride, MLEV_STAT_LOC_RES(n) + L, s); });
       }
       // step 2: glue, then the G_{m+1} problem
-      go(F_GLUE, 24.0 * nfree, [&] { launch_glue(G, P.glay, a, E, mixed ? 1 : 0, s); });
+      go(F_GLUE, 24.0 * nfree, [&] { launch_glue(G, P.glay, a, E, mixed ? 1 : 0, E32, s); });
       const TileList& stop = lp.strip[0];
       if (stop.count) {
         go(F_STRIP_RHS, (32.0 + 2 * t + kfine_extra()) * stop.unk,
            [&] { launch_strip_rhs<T>(G, P.glay, a, tiles_at(stop), stop.count, X, F, X64, s); });
         solve_set<T>(lp.strip, lp.strip_coarsest, o.strip_vcycles, X, F, X64, r, strip_cmode, &lp.strip_f,
-                     lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem);
+                     lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem, false, !direct32);
         if (o.check_residuals) {
           cudaMemsetAsync(jobnorm, 0, P.w_jobnorm.bytes, s);
           go(F_RESNORM, 16.0 * stop.unk,
@@ -514,7 +518,7 @@ struct Launcher {
              [&] { launch_resnorm_finalize(jobnorm, B, P.m, 0, stat, stat_stride, MLEV_STAT_STRIP_RES(n) + L, s); });
         }
         go(F_STRIP_UPD, 24.0 * stop.unk,
-           [&] { launch_strip_update(G, P.glay, a, tiles_at(stop), stop.count, E, mixed ? 1 : 0, s); });
+           [&] { launch_strip_update(G, P.glay, a, tiles_at(stop), stop.count, E, mixed ? 1 : 0, E32, s); });
       }
       // step 3: Rayleigh-Ritz on V_{0H} + span{u~}
       go(F_AUG, (8.0 + kfine_extra()) * nfree,
@@ -640,7 +644,7 @@ struct Launcher {
         LevelArgs as = a;
         as.ut = sbar;
         go(F_STRIP_UPD, 24.0 * stop.unk,
-           [&] { launch_strip_update(G, P.glay, as, tiles_at(stop), stop.count, E, use64, s); });
+           [&] { launch_strip_update(G, P.glay, as, tiles_at(stop), stop.count, E, use64, nullptr, s); });
         go(F_ADJ_FIELD, 24.0 * nfree, [&] { launch_strip_adj_post(G, P.glay, L, B, utbar, sbar, s); });
         go(F_ADJ_GRAD, 16.0 * nfree, [&] { launch_grad_pair(G, P.glay, L, B, -1.0, sbar, utl, gL, s); });
       }

@@ -58,8 +58,10 @@ __global__ void __launch_bounds__(256) k_rhs(DevGeom G, GlobalLayout gl, LevelAr
 }
 
 // Step 2 of Algorithm 4.1: u~ = u_in + e^j on closed G_j, u_in on G_{m+1} (corrected
-// later by the G_{m+1} solve), 0 on dOmega.
-__global__ void __launch_bounds__(256) k_glue(DevGeom G, GlobalLayout gl, LevelArgs a, const double* E, int use64) {
+// later by the G_{m+1} solve), 0 on dOmega. e^j is read from the FP64 pool E, or widened from
+// the FP32 multigrid pool E32 when that holds the whole solution (one pass, mixed precision).
+__global__ void __launch_bounds__(256) k_glue(DevGeom G, GlobalLayout gl, LevelArgs a, const double* E, int use64,
+                                              const float* E32) {
   const int p = blockIdx.z, L = a.L;
   const int i = blockIdx.x * GX + threadIdx.x, j = blockIdx.y * GY + threadIdx.y;
   const int nx = gl.nx[lidx(L)], ny = gl.ny[lidx(L)], pitch = gl.pitch[lidx(L)];
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(256) k_glue(DevGeom G, GlobalLayout gl, LevelA
   if (lab > 0) {
     const GridDesc& g = G.grids[G.sub_top[p * G.m + lab - 1]];
     const long long c = (long long)(j - g.oy) * g.pitch + (i - g.ox);
-    v += E[(use64 ? g.off64 : g.off) + c];
+    v += E32 ? (double)E32[g.off + c] : E[(use64 ? g.off64 : g.off) + c];
   }
   a.ut[idx] = v;
 }
@@ -110,13 +112,14 @@ __global__ void __launch_bounds__(256) k_strip_rhs(DevGeom G, GlobalLayout gl, L
 }
 
 __global__ void __launch_bounds__(256) k_strip_update(DevGeom G, GlobalLayout gl, LevelArgs a, const Tile* __restrict__ tiles,
-                                                      const double* E, int use64) {
+                                                      const double* E, int use64, const float* E32) {
   const Tile t = tiles[blockIdx.x];
   const GridDesc& g = G.grids[t.grid];
   const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
   if (!is_unknown(G, g, i, j)) return;
   const long long c = (long long)j * g.pitch + i;
-  a.ut[(long long)g.problem * gl.bstride + (long long)j * gl.pitch[lidx(g.level)] + i] += E[(use64 ? g.off64 : g.off) + c];
+  a.ut[(long long)g.problem * gl.bstride + (long long)j * gl.pitch[lidx(g.level)] + i] +=
+      E32 ? (double)E32[g.off + c] : E[(use64 ? g.off64 : g.off) + c];
 }
 
 // Step 3 inputs on one T_H cell: alpha = a(u~,u~), beta = b(u~,u~), sigma = sum of u~,
@@ -321,9 +324,9 @@ void launch_interp(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a,
 void launch_rhs(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, cudaStream_t s) {
   MLEV_DISPATCH_KK(G.kap.kind, (k_rhs<KK><<<global_grid(gl, a.L, a.B), dim3(GX, GY), 0, s>>>(G, gl, a)));
 }
-void launch_glue(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const double* E, int use64,
+void launch_glue(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const double* E, int use64, const float* E32,
                  cudaStream_t s) {
-  k_glue<<<global_grid(gl, a.L, a.B), dim3(GX, GY), 0, s>>>(G, gl, a, E, use64);
+  k_glue<<<global_grid(gl, a.L, a.B), dim3(GX, GY), 0, s>>>(G, gl, a, E, use64, E32);
 }
 template <typename T>
 void launch_strip_rhs(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const Tile* tiles, int n, T* X,
@@ -336,9 +339,9 @@ template void launch_strip_rhs<float>(const DevGeom&, const GlobalLayout&, const
 template void launch_strip_rhs<double>(const DevGeom&, const GlobalLayout&, const LevelArgs&, const Tile*, int,
                                        double*, double*, double*, cudaStream_t);
 void launch_strip_update(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const Tile* tiles, int n,
-                         const double* E, int use64, cudaStream_t s) {
+                         const double* E, int use64, const float* E32, cudaStream_t s) {
   if (!n) return;
-  k_strip_update<<<n, dim3(GX, GY), 0, s>>>(G, gl, a, tiles, E, use64);
+  k_strip_update<<<n, dim3(GX, GY), 0, s>>>(G, gl, a, tiles, E, use64, E32);
 }
 template <int KK>
 static void launch_aug_kk(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, double* partials,

@@ -65,14 +65,15 @@ struct LevelArgs {
 };
 void launch_interp(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, cudaStream_t s);
 void launch_rhs(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, cudaStream_t s);
-// glue: E = FP64 local solutions (pool base); use64 selects GridDesc::off64 (mixed) or ::off (FP64 mode)
+// glue: E = FP64 local solutions (pool base); use64 selects GridDesc::off64 (mixed) or ::off (FP64 mode);
+// E32 (nullable) = the FP32 pool, read instead of E when it holds the whole solution
 void launch_glue(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const double* E, int use64,
-                 cudaStream_t s);
+                 const float* E32, cudaStream_t s);
 template <typename T>
 void launch_strip_rhs(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const Tile* tiles, int n, T* X,
                       T* F, double* X64, cudaStream_t s);
 void launch_strip_update(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, const Tile* tiles, int n,
-                         const double* E, int use64, cudaStream_t s);
+                         const double* E, int use64, const float* E32, cudaStream_t s);
 // Rayleigh-Ritz factors prepared by one extra block per batch member of the inner-product
 // kernel (rr_prefactor_block); K_H, M_H [B][nhb][bw+1], out [B][stride].
 struct RRPrefactor {
