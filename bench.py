@@ -329,7 +329,7 @@ def main():
     ny, nx = solver.grid_shape()
     lam_h = torch.empty(p.batch, dtype=torch.float64, pin_memory=True).numpy()
     u_h = torch.empty((p.batch, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
-    oh = mixed_opts(mlev, graph=0)
+    oh = mixed_opts(mlev, graph=1)  # graph replay, as in the device-timed leg
     io = solver.solve_host(oh, lam_h, u_h, report=True)
     solver.solve_host(oh, lam_h, u_h)
     e2e_t = []
@@ -340,6 +340,7 @@ def main():
         solver.solve_host(oh, lam_h, u_h)
         e2e_t.append(time.perf_counter() - t0)
     e2e_ms = replicas.max_over_ranks(1e3 * statistics.mean(e2e_t), dist, "cuda")
+    e2e_lambda = float(lam_h[0])
     h2d, d2h = int(io["h2d_bytes"]), int(io["d2h_bytes"])
 
     # profiled pass: per-kernel-family CUDA-event times on the solve's stream
@@ -398,7 +399,8 @@ def main():
                                                   "speedup_mixed_over_fp64": ms_fp64 / ms_mixed},
         "e2e": {"value": world * n_units / (e2e_ms / 1e3), "unit": "DOF/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "call": "mlev_solve_host (plan tables H2D, solve, lambda + u_{h_n} D2H)"},
+                "call": "mlev_solve_host (plan tables H2D, graph-replayed solve, lambda + u_{h_n} D2H, pinned host buffers)",
+                "lambda_matches_device_path": e2e_lambda == lam_mixed},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "profile": [{k: r[k] for k in ("name", "launches", "ms", "bytes")} for r in prof if r["launches"]],

@@ -140,6 +140,37 @@ def test_host_buffer_entry_point_matches_device_path():
     s.close()
 
 
+@pytest.mark.parametrize("name", ["c2n4", "lshape-n3-seed7"])
+def test_one_pass_direct_read_matches_accumulated_pool(name):
+    """With one refinement pass the glue reads the FP32 multigrid solution directly; the
+    residual-check path accumulates it into the FP64 pool first. Both give the same bits."""
+    from paper_1401_4969_gb300 import mlev
+
+    p = CASES[name]()
+    s = mlev.Solver(p)
+    lam_a, u_a, _ = s.solve(mlev.default_opts(precision=1, refine_passes=1, check_residuals=0), want_u=True)
+    lam_b, u_b, _ = s.solve(mlev.default_opts(precision=1, refine_passes=1, check_residuals=1), want_u=True)
+    s.close()
+    assert np.array_equal(lam_a.cpu().numpy(), lam_b.cpu().numpy())
+    assert np.array_equal(u_a.cpu().numpy(), u_b.cpu().numpy())
+
+
+def test_host_entry_point_with_graph_replay():
+    from paper_1401_4969_gb300 import mlev
+
+    p = W.config2(levels=4)
+    s = mlev.Solver(p)
+    o = mlev.default_opts(precision=1, refine_passes=1, use_graph=1)
+    lam_d, u_d, _ = s.solve(mlev.default_opts(precision=1, refine_passes=1), want_u=True)
+    lam_h = np.zeros(p.batch)
+    u_h = np.zeros((p.batch, *s.grid_shape()))
+    for _ in range(3):  # the first call captures the graph, the others replay it
+        s.solve_host(o, lam_h, u_h)
+        assert np.array_equal(lam_h, lam_d.cpu().numpy())
+        assert np.array_equal(u_h, u_d.cpu().numpy())
+    s.close()
+
+
 def test_graph_replay_matches_stream_launches():
     from paper_1401_4969_gb300 import mlev
 
