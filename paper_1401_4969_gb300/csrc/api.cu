@@ -145,6 +145,9 @@ struct Launcher {
   }
 
   // Enqueue one launch; in profiling mode bracket it with events on the stream.
+  // pre-smoothing by plain Gauss-Seidel ends with the black half-sweep: black residuals vanish
+  int black_zero() const { return o.pre_smooth >= 1 && o.omega == 1.0 ? 1 : 0; }
+
   template <class Fn>
   void go(Fam f, double bytes, Fn&& fn) {
     if (profiling) {
@@ -197,7 +200,7 @@ struct Launcher {
         smooth(d, 1);
       }
       go(F_RESTRICT, (10 * t + 4 * kfine_extra()) * lists[d + 1].unk,
-         [&] { launch_restrict<T>(G, tiles_at(lists[d + 1]), lists[d + 1].count, X, F, s); });
+         [&] { launch_restrict<T>(G, tiles_at(lists[d + 1]), lists[d + 1].count, X, F, black_zero(), s); });
     }
     coarse_solve<T>(cmode, coarsest, X, F);
     for (int d = D - 1; d >= 0; --d) {
@@ -255,7 +258,7 @@ struct Launcher {
         smooth(d, 1);
       }
       go(F_RESTRICT, (10 * t + 4 * kfine_extra()) * lists[d + 1].unk,
-         [&] { launch_restrict<T>(G, tiles_at(lists[d + 1]), lists[d + 1].count, X, F, s); });
+         [&] { launch_restrict<T>(G, tiles_at(lists[d + 1]), lists[d + 1].count, X, F, black_zero(), s); });
     }
     const T* inv = direct ? at<T>(ws, P.w_cinv) : nullptr;
     if (dt == D && !direct && coarsest_smem_bytes(P.kappa_kind, P.strip_coarse_nodes, sizeof(T)) <= 220 * 1024) {

@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
     __syncthreads();
     for (int d = 0; d + 1 < nlev; ++d) {
       tail_smooth<T, KK>(G, lv[d], a.pre, false, (T)a.omega);
-      tail_restrict<T, KK>(G, lv[d], lv[d + 1]);
+      tail_restrict<T, KK>(G, lv[d], lv[d + 1], a.pre >= 1 && a.omega == 1.0);
     }
     tail_smooth<T, KK>(G, lv[nlev - 1], a.coarse_sweeps, false, (T)a.omega);
     for (int d = nlev - 2; d >= 0; --d) {

@@ -11,7 +11,8 @@ template <typename T>
 void launch_smooth(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, int color, double omega,
                    cudaStream_t s);
 template <typename T>
-void launch_restrict(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, cudaStream_t s);
+// black_zero: the fine grid's last half-sweep was black with omega = 1 (k_restrict)
+void launch_restrict(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, int black_zero, cudaStream_t s);
 template <typename T>
 void launch_prolong(const DevGeom& G, const Tile* tiles, int n, T* X, cudaStream_t s);
 template <typename T>

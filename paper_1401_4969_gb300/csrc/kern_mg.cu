@@ -40,9 +40,14 @@ __device__ __forceinline__ T residual_at(const DevGeom& G, const GridDesc& g, co
   return F[g.off + c] - apply_k<T, T>(X + g.off, c, g.pitch, w);
 }
 
-// Coarse grid (tiles over depth d+1): f_c = P^T (f - A x)_fine, x_c = 0.
+// Coarse grid (tiles over depth d+1): f_c = P^T (f - A x)_fine, x_c = 0. With `black_zero`
+// the fine grid was just pre-smoothed by plain Gauss-Seidel (omega = 1) ending with the black
+// half-sweep: the residual of every black node (odd i + j) is then zero, since each was
+// relaxed against its red neighbours and black nodes do not couple, so of the seven fine
+// nodes of the coarse hat only the red ones (the node itself, NE and SW) contribute.
 template <typename T, int KK>
-__global__ void __launch_bounds__(256) k_restrict(DevGeom G, const Tile* __restrict__ tiles, T* X, T* F) {
+__global__ void __launch_bounds__(256) k_restrict(DevGeom G, const Tile* __restrict__ tiles, T* X, T* F,
+                                                  int black_zero) {
   const Tile t = tiles[blockIdx.x];
   const GridDesc& gc = G.grids[t.grid];
   const GridDesc& gf = G.grids[t.grid - 1];
@@ -53,9 +58,10 @@ __global__ void __launch_bounds__(256) k_restrict(DevGeom G, const Tile* __restr
   if (!is_unknown(G, gc, I, J)) return;
   const int i = 2 * I, j = 2 * J;
   T acc = residual_at<T, KK>(G, gf, X, F, i, j);
-  T half = residual_at<T, KK>(G, gf, X, F, i + 1, j) + residual_at<T, KK>(G, gf, X, F, i - 1, j) +
-           residual_at<T, KK>(G, gf, X, F, i, j + 1) + residual_at<T, KK>(G, gf, X, F, i, j - 1) +
-           residual_at<T, KK>(G, gf, X, F, i + 1, j + 1) + residual_at<T, KK>(G, gf, X, F, i - 1, j - 1);
+  T half = residual_at<T, KK>(G, gf, X, F, i + 1, j + 1) + residual_at<T, KK>(G, gf, X, F, i - 1, j - 1);
+  if (!black_zero)
+    half += residual_at<T, KK>(G, gf, X, F, i + 1, j) + residual_at<T, KK>(G, gf, X, F, i - 1, j) +
+            residual_at<T, KK>(G, gf, X, F, i, j + 1) + residual_at<T, KK>(G, gf, X, F, i, j - 1);
   F[gc.off + cc] = acc + (T)0.5 * half;
 }
 
@@ -349,9 +355,9 @@ void launch_smooth(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F,
   MLEV_DISPATCH_KK(G.kap.kind, (k_smooth<T, KK><<<n, dim3(TX, TY), 0, s>>>(G, tiles, X, F, color, (T)omega)));
 }
 template <typename T>
-void launch_restrict(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, cudaStream_t s) {
+void launch_restrict(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, int black_zero, cudaStream_t s) {
   if (!n) return;
-  MLEV_DISPATCH_KK(G.kap.kind, (k_restrict<T, KK><<<n, dim3(TX, TY), 0, s>>>(G, tiles, X, F)));
+  MLEV_DISPATCH_KK(G.kap.kind, (k_restrict<T, KK><<<n, dim3(TX, TY), 0, s>>>(G, tiles, X, F, black_zero)));
 }
 template <typename T>
 void launch_prolong(const DevGeom& G, const Tile* tiles, int n, T* X, cudaStream_t s) {
@@ -433,7 +439,7 @@ void launch_resnorm_finalize(const double* acc, int B, int m, int subdomains, lo
 
 #define MLEV_INST(T)                                                                                             \
   template void launch_smooth<T>(const DevGeom&, const Tile*, int, T*, const T*, int, double, cudaStream_t);     \
-  template void launch_restrict<T>(const DevGeom&, const Tile*, int, T*, T*, cudaStream_t);                      \
+  template void launch_restrict<T>(const DevGeom&, const Tile*, int, T*, T*, int, cudaStream_t);                 \
   template void launch_prolong<T>(const DevGeom&, const Tile*, int, T*, cudaStream_t);                           \
   template void launch_coarsest<T>(const DevGeom&, const Tile*, int, T*, const T*, int, double, cudaStream_t);   \
   template void launch_gather<T>(const DevGeom&, const GlobalLayout&, const Tile*, int, T*, T*, double*,         \

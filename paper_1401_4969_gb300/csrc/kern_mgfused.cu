@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(512) k_mg_tail(DevGeom G, const Tile* __restri
   const T* jinv = inv ? inv + (long long)lv[0].g->job * nd_max * nd_max : nullptr;
   for (int d = 0; d + 1 < nlev; ++d) {
     tail_smooth<T, KK>(G, lv[d], pre, false, omega);
-    tail_restrict<T, KK>(G, lv[d], lv[d + 1]);
+    tail_restrict<T, KK>(G, lv[d], lv[d + 1], pre >= 1 && omega == (T)1);
   }
   if (jinv)
     tail_direct<T>(lv[nlev - 1], jinv, fbuf);

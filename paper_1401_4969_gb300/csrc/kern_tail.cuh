@@ -52,17 +52,20 @@ __device__ __forceinline__ T tail_res(const DevGeom& G, const SmGrid<T>& s, int 
                    (T)w.n * s.x[q + s.W] - (T)w.s * s.x[q - s.W]);
 }
 
+// f_c = P^T (f - A x)_fine, x_c = 0; black_zero as in k_restrict (pre-smoothed by plain
+// Gauss-Seidel ending black: only the red nodes of the coarse hat have a residual).
 template <typename T, int KK>
-__device__ void tail_restrict(const DevGeom& G, const SmGrid<T>& fi, const SmGrid<T>& co) {
+__device__ void tail_restrict(const DevGeom& G, const SmGrid<T>& fi, const SmGrid<T>& co, bool black_zero) {
   for (int J = threadIdx.y; J <= co.ny; J += blockDim.y)
     for (int I = threadIdx.x; I <= co.nx; I += blockDim.x) {
       const int q = J * co.W + I;
       co.x[q] = (T)0;
       if (!co.m[q]) continue;
       const int i = 2 * I, j = 2 * J;
-      const T half = tail_res<T, KK>(G, fi, i + 1, j) + tail_res<T, KK>(G, fi, i - 1, j) +
-                     tail_res<T, KK>(G, fi, i, j + 1) + tail_res<T, KK>(G, fi, i, j - 1) +
-                     tail_res<T, KK>(G, fi, i + 1, j + 1) + tail_res<T, KK>(G, fi, i - 1, j - 1);
+      T half = tail_res<T, KK>(G, fi, i + 1, j + 1) + tail_res<T, KK>(G, fi, i - 1, j - 1);
+      if (!black_zero)
+        half += tail_res<T, KK>(G, fi, i + 1, j) + tail_res<T, KK>(G, fi, i - 1, j) +
+                tail_res<T, KK>(G, fi, i, j + 1) + tail_res<T, KK>(G, fi, i, j - 1);
       co.f[q] = tail_res<T, KK>(G, fi, i, j) + (T)0.5 * half;
     }
   __syncthreads();
