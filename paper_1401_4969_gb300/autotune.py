@@ -33,7 +33,7 @@ FLOAT_KEYS = ("level1_tol",)
 # A schedule is accepted when every eigenvalue is within SAFETY * target_rel of the reference
 # (a 4x margin to the target for what the reference itself and other inputs may add).
 SAFETY = 0.25
-LEVEL1_TOLS = (1e-8, 1e-6, 1e-4, 1e-3)  # level-1 residual targets tried, tightest first
+LEVEL1_TOLS = (1e-8, 1e-6, 1e-4, 1e-3, 1e-2)  # level-1 residual targets tried, tightest first
 
 
 def default_cache_path() -> str:
@@ -122,7 +122,7 @@ def search(evaluate, target_rel: float, safety: float = SAFETY, base: dict | Non
         raise RuntimeError(f"no schedule reached relative error {tol:g}; best trials: "
                            f"{sorted(trials, key=lambda t: t.err)[:3]}")
     best = min(accepted, key=lambda t: t.ms)
-    for key, values in (("coarse_sweeps", (20, 10)), ("pre_smooth", (1,)), ("post_smooth", (1,)),
+    for key, values in (("coarse_sweeps", (20, 10, 5)), ("pre_smooth", (1,)), ("post_smooth", (1,)),
                         ("level1_tol", LEVEL1_TOLS)):
         for v in values:
             t = run({**best.opts, key: v})

@@ -24,7 +24,8 @@ def test_search_picks_the_fastest_schedule_within_target():
     assert err <= bar
     # no accepted trial is faster than the result
     assert min(t.ms for t in res.trials if t.ok) == pytest.approx(res.ms)
-    assert res.opts["fused"] == 1 and res.opts["coarse_sweeps"] == 10
+    # the model's error does not depend on the coarsest sweeps: the cheapest candidate wins
+    assert res.opts["fused"] == 1 and res.opts["coarse_sweeps"] == 5
     # the level-1 target was loosened, and the next looser candidate broke the bar
     chosen = res.opts["level1_tol"]
     assert chosen in AT.LEVEL1_TOLS
