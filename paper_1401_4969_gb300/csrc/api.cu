@@ -147,6 +147,8 @@ struct Launcher {
   // Enqueue one launch; in profiling mode bracket it with events on the stream.
   // pre-smoothing by plain Gauss-Seidel ends with the black half-sweep: black residuals vanish
   int black_zero() const { return o.pre_smooth >= 1 && o.omega == 1.0 ? 1 : 0; }
+  // post-smoothing starts with a plain Gauss-Seidel black half-sweep: black nodes need no correction
+  int red_only() const { return o.post_smooth >= 1 && o.omega == 1.0 ? 1 : 0; }
 
   template <class Fn>
   void go(Fam f, double bytes, Fn&& fn) {
@@ -204,7 +206,8 @@ struct Launcher {
     }
     coarse_solve<T>(cmode, coarsest, X, F);
     for (int d = D - 1; d >= 0; --d) {
-      go(F_PROLONG, 2.25 * t * lists[d].unk, [&] { launch_prolong<T>(G, tiles_at(lists[d]), lists[d].count, X, s); });
+      go(F_PROLONG, 2.25 * t * lists[d].unk,
+         [&] { launch_prolong<T>(G, tiles_at(lists[d]), lists[d].count, X, red_only(), s); });
       for (int k = 0; k < o.post_smooth; ++k) {
         smooth(d, 1);
         smooth(d, 0);
@@ -273,7 +276,8 @@ struct Launcher {
       });
     }
     for (int d = dt - 1; d >= 0; --d) {
-      go(F_PROLONG, 2.25 * t * lists[d].unk, [&] { launch_prolong<T>(G, tiles_at(lists[d]), lists[d].count, X, s); });
+      go(F_PROLONG, 2.25 * t * lists[d].unk,
+         [&] { launch_prolong<T>(G, tiles_at(lists[d]), lists[d].count, X, red_only(), s); });
       for (int k = 0; k < o.post_smooth; ++k) {
         smooth(d, 1);
         smooth(d, 0);

@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
     }
     tail_smooth<T, KK>(G, lv[nlev - 1], a.coarse_sweeps, false, (T)a.omega);
     for (int d = nlev - 2; d >= 0; --d) {
-      tail_prolong<T>(lv[d], lv[d + 1]);
+      tail_prolong<T>(lv[d], lv[d + 1], a.post >= 1 && a.omega == 1.0);
       tail_smooth<T, KK>(G, lv[d], a.post, true, (T)a.omega);
     }
     for (int q = tid; q < nn; q += nt) Wv[q] = (float)lv[0].x[q];

@@ -14,7 +14,8 @@ template <typename T>
 // black_zero: the fine grid's last half-sweep was black with omega = 1 (k_restrict)
 void launch_restrict(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, int black_zero, cudaStream_t s);
 template <typename T>
-void launch_prolong(const DevGeom& G, const Tile* tiles, int n, T* X, cudaStream_t s);
+// red_only: the next half-sweep is black with omega = 1 (k_prolong)
+void launch_prolong(const DevGeom& G, const Tile* tiles, int n, T* X, int red_only, cudaStream_t s);
 template <typename T>
 void launch_coarsest(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, int sweeps, double omega,
                      cudaStream_t s);

@@ -65,14 +65,16 @@ __global__ void __launch_bounds__(256) k_restrict(DevGeom G, const Tile* __restr
   F[gc.off + cc] = acc + (T)0.5 * half;
 }
 
-// Fine grid (tiles over depth d): x += P x_c.
+// Fine grid (tiles over depth d): x += P x_c. With `red_only` the post-smoothing that follows
+// starts with a plain Gauss-Seidel (omega = 1) black half-sweep, which sets every black node
+// from its red neighbours alone, so only the red nodes take the correction.
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong(DevGeom G, const Tile* __restrict__ tiles, T* X) {
+__global__ void __launch_bounds__(256) k_prolong(DevGeom G, const Tile* __restrict__ tiles, T* X, int red_only) {
   const Tile t = tiles[blockIdx.x];
   const GridDesc& gf = G.grids[t.grid];
   const GridDesc& gc = G.grids[t.grid + 1];
   const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
-  if (!is_unknown(G, gf, i, j)) return;
+  if ((red_only && ((i + j) & 1)) || !is_unknown(G, gf, i, j)) return;
   const T* xc = X + gc.off;
   const int I = i >> 1, J = j >> 1;
   T v;
@@ -360,9 +362,9 @@ void launch_restrict(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, int
   MLEV_DISPATCH_KK(G.kap.kind, (k_restrict<T, KK><<<n, dim3(TX, TY), 0, s>>>(G, tiles, X, F, black_zero)));
 }
 template <typename T>
-void launch_prolong(const DevGeom& G, const Tile* tiles, int n, T* X, cudaStream_t s) {
+void launch_prolong(const DevGeom& G, const Tile* tiles, int n, T* X, int red_only, cudaStream_t s) {
   if (!n) return;
-  k_prolong<T><<<n, dim3(TX, TY), 0, s>>>(G, tiles, X);
+  k_prolong<T><<<n, dim3(TX, TY), 0, s>>>(G, tiles, X, red_only);
 }
 template <typename T>
 void launch_coarsest(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, int sweeps, double omega,
@@ -440,7 +442,7 @@ void launch_resnorm_finalize(const double* acc, int B, int m, int subdomains, lo
 #define MLEV_INST(T)                                                                                             \
   template void launch_smooth<T>(const DevGeom&, const Tile*, int, T*, const T*, int, double, cudaStream_t);     \
   template void launch_restrict<T>(const DevGeom&, const Tile*, int, T*, T*, int, cudaStream_t);                 \
-  template void launch_prolong<T>(const DevGeom&, const Tile*, int, T*, cudaStream_t);                           \
+  template void launch_prolong<T>(const DevGeom&, const Tile*, int, T*, int, cudaStream_t);                      \
   template void launch_coarsest<T>(const DevGeom&, const Tile*, int, T*, const T*, int, double, cudaStream_t);   \
   template void launch_gather<T>(const DevGeom&, const GlobalLayout&, const Tile*, int, T*, T*, double*,         \
                                  const double*, cudaStream_t);                                                   \

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(512) k_mg_tail(DevGeom G, const Tile* __restri
   else
     tail_smooth<T, KK>(G, lv[nlev - 1], csweeps, false, omega);
   for (int d = nlev - 2; d >= 0; --d) {
-    tail_prolong<T>(lv[d], lv[d + 1]);
+    tail_prolong<T>(lv[d], lv[d + 1], post >= 1 && omega == (T)1);
     tail_smooth<T, KK>(G, lv[d], post, true, omega);
   }
   const GridDesc& g0 = *lv[0].g;

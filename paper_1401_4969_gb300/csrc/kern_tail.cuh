@@ -71,12 +71,13 @@ __device__ void tail_restrict(const DevGeom& G, const SmGrid<T>& fi, const SmGri
   __syncthreads();
 }
 
+// x += P x_c; red_only as in k_prolong (the next half-sweep is black with omega = 1).
 template <typename T>
-__device__ void tail_prolong(const SmGrid<T>& fi, const SmGrid<T>& co) {
+__device__ void tail_prolong(const SmGrid<T>& fi, const SmGrid<T>& co, bool red_only) {
   for (int j = 1 + threadIdx.y; j < fi.ny; j += blockDim.y)
     for (int i = 1 + threadIdx.x; i < fi.nx; i += blockDim.x) {
       const int q = j * fi.W + i;
-      if (!fi.m[q]) continue;
+      if (!fi.m[q] || (red_only && ((i + j) & 1))) continue;
       const int I = i >> 1, J = j >> 1, c = J * co.W + I;
       T v;
       if (!(i & 1) && !(j & 1)) v = co.x[c];
