@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(256) k_rr(DevGeom G, RRArgs a) {
 // w^T S^{-1} w, whose error is quadratic in the error of y.
 __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   extern __shared__ double rr_sm[];
-  __shared__ double scratch[8 * 4];
+  __shared__ double stage[4 * 256];  // FP64 block sums, one warp per quantity (block_sum_t)
   __shared__ double red[4];
   __shared__ int bflag;
   const int p = blockIdx.x, N = a.nhb, bw = a.bw, bw1 = bw + 1;
@@ -880,7 +880,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
       v[1] += part[q * 12 + 1];
       v[2] += part[q * 12 + 2];
     }
-    block_sum<3>(v, scratch, red);
+    block_sum_t<3>(v, stage, red);
   }
   const double alpha = red[0], beta = red[1], sigma = red[2];
   for (int q = threadIdx.x; q < N; q += blockDim.x) {
@@ -965,7 +965,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
       v[0] += rq * rq;
       v[1] += wv[q] * wv[q];
     }
-    block_sum<2>(v, scratch, red);
+    block_sum_t<2>(v, stage, red);
     return red[1] > 0.0 ? red[0] / red[1] : 0.0;
   };
   // refine to rel^2 <= target; false if the iteration stalls first (then refactor at mu)
@@ -988,7 +988,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
       v[2] += gb[q] * y[q];
       v[3] += y[q] * band_mv(MH, y, q);
     }
-    block_sum<4>(v, scratch, red);
+    block_sum_t<4>(v, stage, red);
     f = alpha - mu * beta - (red[0] + red[1]);
     fp = -beta + 2.0 * red[2] - red[3];
   };
@@ -1003,7 +1003,11 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     const unsigned char* pp = a.pre + (long long)p * a.pre_stride;
     if (*reinterpret_cast<const int*>(pp + 8)) {
       const float* src = reinterpret_cast<const float*>(pp + 16);
-      for (long long q = threadIdx.x; q < 3 * tiles; q += blockDim.x) Dinv[q] = src[q];
+      // float4 copies, several in flight per thread (L2 latency, not bandwidth, bounds this)
+      const float4* s4 = reinterpret_cast<const float4*>(src);
+      float4* d4 = reinterpret_cast<float4*>(Dinv);
+#pragma unroll 4
+      for (long long q = threadIdx.x; q < 3 * tiles / 4; q += blockDim.x) d4[q] = s4[q];
       sig = *reinterpret_cast<const double*>(pp);
       factored = true;
     }
@@ -1062,7 +1066,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     v[1] += gb[q] * y[q];
     v[2] += y[q];
   }
-  block_sum<3>(v, scratch, red);
+  block_sum_t<3>(v, stage, red);
   const double bn = red[0] - 2.0 * red[1] + beta;
   const double S = (double)(1LL << (2 * a.L));
   const double integral = sigma - S * red[2];
