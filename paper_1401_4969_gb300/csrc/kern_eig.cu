@@ -839,9 +839,20 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   const double* KH = a.KH + (long long)p * N * bw1;
   const double* MH = a.MH + (long long)p * N * bw1;
   if (a.smem) {
-    for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) {
-      kh_s[q] = KH[q];
-      mh_s[q] = MH[q];
+    if (a.blocked && bw >= 3) {
+      // only the nonzero diagonals d = 0, 1, b, b + 1 are read in blocked mode (products,
+      // S(mu), the block factor): stage those, independent loads several per thread
+#pragma unroll 4
+      for (int q = threadIdx.x; q < 4 * N; q += blockDim.x) {
+        const long long e = (long long)(q >> 2) * bw1 + coarse_band_diag(q & 3, bw - 1);
+        kh_s[e] = KH[e];
+        mh_s[e] = MH[e];
+      }
+    } else {
+      for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) {
+        kh_s[q] = KH[q];
+        mh_s[q] = MH[q];
+      }
     }
     KH = kh_s;
     MH = mh_s;
