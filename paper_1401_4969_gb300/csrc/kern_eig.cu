@@ -1010,7 +1010,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   int it = 0, status = 0;
   bool have = false, factored = false;
   if (a.use_pre && a.blocked && a.smem) {
-    // factors of S(sigma) prepared while this level's local problems ran (k_rr_prefactor)
+    // factors of S(sigma) prepared by the inner-product kernel just before (rr_prefactor_block)
     const unsigned char* pp = a.pre + (long long)p * a.pre_stride;
     if (*reinterpret_cast<const int*>(pp + 8)) {
       const float* src = reinterpret_cast<const float*>(pp + 16);
