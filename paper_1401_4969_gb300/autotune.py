@@ -33,7 +33,7 @@ FLOAT_KEYS = ("level1_tol",)
 # A schedule is accepted when every eigenvalue is within SAFETY * target_rel of the reference
 # (a 4x margin to the target for what the reference itself and other inputs may add).
 SAFETY = 0.25
-LEVEL1_TOLS = (1e-8, 1e-6, 1e-4, 1e-3, 1e-2)  # level-1 residual targets tried, tightest first
+LEVEL1_TOLS = (1e-8, 1e-6, 1e-4, 1e-3, 1e-2, 3e-2, 1e-1)  # level-1 residual targets tried, tightest first
 
 
 def default_cache_path() -> str:
