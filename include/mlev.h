@@ -190,6 +190,9 @@ int mlev_solve(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_
  * mlev_set_forms, may be NULL to keep the current coefficients) to the device,
  * solves, and copies lambda (and u if u_host != NULL) back, synchronizing stream.
  * The kappa staging area is part of the workspace (mlev_workspace_size counts it).
+ * opts.use_graph applies as in mlev_solve (the plan tables and kappa are copied before
+ * the graph launch, the results after it). Host buffers in pinned memory make the copies
+ * direct transfers.
  */
 int mlev_solve_host(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
                     const double* kappa_host, double* lambda_host, double* u_host, mlev_report* rep);
