@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -301,8 +302,8 @@ def main():
     om = mixed_opts(mlev)
     rep = solver.solve_into(mixed_opts(mlev, graph=0), lam, None, stream, report=True)
     launches_per_step = rep["kernel_launches"]
-    clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/bench_clocks_r{rank}.csv"
+    # nvidia-smi samples of the timed region (MLEV_BENCH_OUT: keep them in that directory)
+    clk_path = os.path.join(os.environ.get("MLEV_BENCH_OUT", tempfile.gettempdir()), f"bench_clocks_r{rank}.csv")
     sampler, fh = start_clock_sampler(clk_path)
     ms_mixed = timed(om, args.steps, args.warmup)
     clocks = stop_clock_sampler(sampler, fh, clk_path, local_rank)
