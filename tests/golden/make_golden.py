@@ -1,8 +1,11 @@
 """Write the oracle's results for the full-size workloads to tests/golden/*.json.
 
 Calls only the CPU oracle (oracle/) on the seeded inputs of workloads/; nothing here
-comes from the CUDA path. Each file holds lambda_{h_k} for k = 1..n and u_{h_n} sampled
-on a coarse sub-lattice (every `stride`-th node in x and y); the gradient file holds the
+comes from the CUDA path. Each file holds lambda_{h_k} for k = 1..n, u_{h_n} sampled
+on a coarse sub-lattice (every `stride`-th node in x and y) and the moments
+(phi_i, u_{h_n}) = b(phi_i, u_{h_n}) of u_{h_n} against every hat function phi_i of the
+level-`MOMENT_LEVEL` mesh (a whole-field pin: every fine node enters some moment); the
+gradient file holds the
 oracle adjoint dlambda_{h_n}/dkappa on 20 seeded finest triangles, its maximum modulus and
 the Euler sum sum_e kappa_e g_e.
 
@@ -23,17 +26,34 @@ import workloads as W  # noqa: E402
 from oracle import multilevel as ML  # noqa: E402
 
 
-def record(p, members, stride):
-    out = {"problem": p.name, "levels": p.levels, "batch": p.batch, "stride": stride, "members": {}}
+MOMENT_LEVEL = 2
+
+
+def hat_moments(hier, n, u_grid, level=MOMENT_LEVEL):
+    """b(phi_i, u) for the hats phi_i of the free nodes of T_{h_level}, u a level-n nodal grid."""
+    lv = hier.levels[n]
+    u = u_grid.ravel()[lv.key(lv.pts)]
+    v = hier.M[n] @ u
+    for k in range(n - 1, level - 1, -1):  # apply the transposed embeddings, level n -> level
+        v = hier.interp[k].T @ v
+    return v[ML.free(hier, level)]
+
+
+def record(p, members, stride, moments=True):
+    out = {"problem": p.name, "levels": p.levels, "batch": p.batch, "stride": stride, "members": {},
+           "moment_level": MOMENT_LEVEL if moments else None}
     for b in members:
         t = time.time()
-        r = ML.solve(p, b=b)
+        hier = ML.build(p, b=b)
+        r = ML.solve(p, b=b, hier=hier)
         out["members"][str(b)] = {
             "lam": r.lam,
             "lam_levels": r.lam_levels,
             "u_samples": r.u[::stride, ::stride].tolist(),
             "oracle_seconds": time.time() - t,
         }
+        if moments:
+            out["members"][str(b)]["moments"] = hat_moments(hier, p.levels, r.u).tolist()
         print(p.name, b, r.lam, "%.1fs" % (time.time() - t), flush=True)
     return out
 
@@ -61,6 +81,8 @@ JOBS = {
     "c4": lambda: record(W.config4(), list(range(0, 256, 37)), 16),
     "c5": lambda: record(W.config5(), [0], 32),
     "c3n5": lambda: record(W.config3(levels=5), [0], 32),
+    "c3n6": lambda: record(W.config3(levels=6), [0], 64),
+    "c3": lambda: record(W.config3(), [0], 256, moments=False),
     "grad_c5": lambda: record_grad(W.config5()),
 }
 
