@@ -201,17 +201,24 @@ int mlev_solve_host(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_
  * Same computation as mlev_solve, for callers that cannot allocate device memory: for
  * example a plugin inside a host application whose own memory pool must own every
  * device allocation, or a latency-critical loop that may never enter the CUDA
- * allocator (cudaMalloc can block and synchronize the device). Nothing in this call
- * allocates: its workspace is a fixed array of MLEV_NOALLOC_WORKSPACE_BYTES (32 MiB)
- * compiled into the library, which every GPU that loads the library keeps until the
- * process exits. The paper has no counterpart; this is an interface convenience.
+ * allocator (cudaMalloc can block and synchronize the device). No device memory is
+ * allocated for data: the workspace is a fixed array of MLEV_NOALLOC_WORKSPACE_BYTES
+ * (32 MiB) compiled into the library, which every GPU that loads the library keeps until
+ * the process exits. The paper has no counterpart; this is an interface convenience.
  *  - Problems whose mlev_workspace_size exceeds MLEV_NOALLOC_WORKSPACE_BYTES are
  *    rejected with MLEV_ENOMEM and a message giving both sizes.
  *  - The first call on a device looks up the array's device address (a one-time
  *    set-up with that device current); make that first call before any stream capture.
- *  - All calls share the one array and each call overwrites it (plan tables are copied
- *    in again every call), so calls whose GPU work overlaps in time (other streams,
- *    other threads or contexts on the same device) race and give wrong results.
+ *    The address is kept for the life of the process, so resetting the device
+ *    (cudaDeviceReset) after that first call is not supported.
+ *  - A call copies the plan tables (and host kappa) into the array and synchronizes
+ *    `stream` only when the array does not already hold this context's tables for its
+ *    current setup (first call, another context used the array since, or a mlev_set_*
+ *    call changed the setup); otherwise it only enqueues the solve.
+ *  - All calls share the one array, so calls whose GPU work overlaps in time (other
+ *    streams, other threads or contexts on the same device) race and give wrong results.
+ *  - opts.use_graph = 1 and opts.profile = 1 create driver objects on first use, as in
+ *    mlev_solve (a private capture stream and a graph executable; CUDA events).
  *  - Outputs and the meaning of every argument are as in mlev_solve.
  */
 #define MLEV_NOALLOC_WORKSPACE_BYTES (32u << 20)

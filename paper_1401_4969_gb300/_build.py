@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libmlev.so")
-SOURCES = ["plan.cpp", "kern_mg.cu", "kern_mgfused.cu", "kern_field.cu", "kern_eig.cu", "kern_adj.cu", "api.cu"]
+SOURCES = ["plan.cpp", "kern_mg.cu", "kern_mgfused.cu", "kern_mgreg.cu", "kern_field.cu", "kern_eig.cu", "kern_adj.cu", "api.cu"]
 HEADERS = ["mlev_internal.h", "plan.h", "kern_common.cuh", "kern_launch.h", "kern_blk.cuh", "kern_band.cuh",
            "kern_coarse.cuh", "kern_tail.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -49,8 +49,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     cc = nvcc()
     flags = FLAGS + (extra_flags or [])
 
+    common = [os.path.join(CSRC, f) for f in HEADERS] + [os.path.join(ROOT, "include", "mlev.h"), __file__]
+    newest_common = max(os.path.getmtime(d) for d in common)
+
     def compile_one(src):
         obj = os.path.join(OUT, "obj", src + ".o")
+        if (not force and not extra_flags and os.path.exists(obj) and
+                os.path.getmtime(obj) >= max(newest_common, os.path.getmtime(os.path.join(CSRC, src)))):
+            return obj  # object newer than its source and every header
         cmd = [cc, *ARCH, *flags, "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -24,6 +26,7 @@ struct ProfRecHost {
 
 struct mlev_ctx {
   int device = 0;
+  unsigned long long uid = 0;  // unique per context for the life of the process (never reused)
   int sm_count = 0, smem_per_sm = 0;  // device attributes (launch-shape decisions)
   Plan plan;
   std::string err;
@@ -31,7 +34,6 @@ struct mlev_ctx {
   const void* uploaded_ws = nullptr;
   long long uploaded_version = -1;
   long long version = 0;
-  bool kappa_dirty = true;
   // captured graph (captured on a private stream: the legacy default stream cannot capture)
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -52,6 +54,8 @@ struct mlev_ctx {
 
 namespace {
 
+std::atomic<unsigned long long> g_next_ctx_uid{1};
+
 int fail(mlev_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -66,6 +70,34 @@ int cuda_fail(mlev_ctx* c, cudaError_t e, const char* where) {
     cudaError_t _e = (call);                          \
     if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
   } while (0)
+
+// No C++ exception crosses the C interface: every entry point turns a host allocation
+// failure into MLEV_ENOMEM and any other exception into MLEV_EINVAL.
+#define MLEV_TRY try {
+#define MLEV_CATCH(c)                                                         \
+  }                                                                           \
+  catch (const std::bad_alloc&) {                                             \
+    return fail(c, MLEV_ENOMEM, "host allocation failed");                    \
+  }                                                                           \
+  catch (const std::exception& _ex) {                                         \
+    return fail(c, MLEV_EINVAL, std::string("internal error: ") + _ex.what()); \
+  }                                                                           \
+  catch (...) {                                                               \
+    return fail(c, MLEV_EINVAL, "internal error");                            \
+  }
+
+// Host-side fault injection for the error-path tests: MLEV_FAULT holds a comma-separated
+// list of sites. Nothing here touches the GPU in a way that can fault or hang it.
+//   plan_alloc  the planner's host allocation fails          -> MLEV_ENOMEM
+//   h2d_copy    the copy of the plan tables to the device fails -> MLEV_ECUDA
+//   kappa_nan   one staged coefficient value becomes NaN after validation, so the device
+//               computation meets a non-finite value          -> MLEV_ENOCONV
+bool fault_armed(const char* site) {
+  const char* v = std::getenv("MLEV_FAULT");
+  if (!v || !*v) return false;
+  const std::string list = std::string(",") + v + ",";
+  return list.find(std::string(",") + site + ",") != std::string::npos;
+}
 
 int map_plan_error(mlev_ctx* ctx, const std::string& e) {
   if (e.empty()) return MLEV_OK;
@@ -217,13 +249,31 @@ struct Launcher {
 
   // One V-cycle with the fused kernels: down (smooth + restrict) on the depths above the
   // tail, the tail (rest of the cycle in shared memory, one block per job), then up.
+  // the register-blocked FP32 down / up kernels replace the shared-memory ones where they apply
+  template <typename T>
+  bool use_reg(const std::vector<TileList>* rl) const {
+    return sizeof(T) == 4 && rl && rkernels_support(P.kappa_kind, o.pre_smooth, o.post_smooth);
+  }
+
   template <typename T>
   void vcycle_fused(const std::vector<TileList>& fl, int dt, int D, const TileList& tail, size_t tail_smem, T* X, T* F,
-                    bool direct) {
+                    bool direct, const std::vector<TileList>* rl = nullptr, const std::vector<int>* rfull = nullptr) {
     const double t = sizeof(T);
-    for (int d = 0; d < dt; ++d)
+    const bool reg = use_reg<T>(rl);
+    float* XS = at<float>(ws, P.w_xs);
+    for (int d = 0; d < dt; ++d) {
+      if constexpr (sizeof(T) == 4) {
+        if (reg) {
+          const TileList& tl = (*rl)[d];
+          go(F_MG_DOWN, (3.5 * t + o.pre_smooth * kfine_extra()) * tl.unk, [&] {
+            launch_rdown(G, tiles_at(tl), tl.count, (*rfull)[d], X, XS, F, o.pre_smooth, o.omega, black_zero(), s);
+          });
+          continue;
+        }
+      }
       go(F_MG_DOWN, (3.5 * t + o.pre_smooth * kfine_extra()) * fl[d].unk,
          [&] { launch_mg_down<T>(G, tiles_at(fl[d]), fl[d].count, X, F, o.pre_smooth, o.omega, s); });
+    }
     const T* inv = direct ? at<T>(ws, P.w_cinv) : nullptr;
     if (dt == D && !direct &&
         coarsest_smem_bytes(P.kappa_kind, P.strip_coarse_nodes, sizeof(T)) <= 220 * 1024) {
@@ -240,9 +290,19 @@ struct Launcher {
                           o.pre_smooth, o.post_smooth, o.coarse_sweeps, o.omega, dt == 0 ? 1 : 0, tail_smem, s);
       });
     }
-    for (int d = dt - 1; d >= 0; --d)
+    for (int d = dt - 1; d >= 0; --d) {
+      if constexpr (sizeof(T) == 4) {
+        if (reg) {
+          const TileList& tl = (*rl)[d];
+          go(F_MG_UP, (3.25 * t + o.post_smooth * kfine_extra()) * tl.unk, [&] {
+            launch_rup(G, tiles_at(tl), tl.count, (*rfull)[d], XS, X, F, o.post_smooth, o.omega, red_only(), s);
+          });
+          continue;
+        }
+      }
       go(F_MG_UP, (3.25 * t + o.post_smooth * kfine_extra()) * fl[d].unk,
          [&] { launch_mg_up<T>(G, tiles_at(fl[d]), fl[d].count, X, F, o.post_smooth, o.omega, s); });
+    }
   }
 
   // Hybrid V-cycle (opts.fused = 2): one launch per operation on the depths above the tail
@@ -289,7 +349,8 @@ struct Launcher {
   template <typename T>
   void solve_set(const std::vector<TileList>& lists, const TileList& coarsest, int vcycles, T* X, T* F, double* X64,
                  const double* R, int cmode, const std::vector<TileList>* fl = nullptr, int dt = 0,
-                 const TileList* tail = nullptr, size_t tail_smem = 0, bool rmask = false, bool accum_out = true) {
+                 const TileList* tail = nullptr, size_t tail_smem = 0, bool rmask = false, bool accum_out = true,
+                 const std::vector<TileList>* rl = nullptr, const std::vector<int>* rfull = nullptr) {
     const int D = (int)lists.size() - 1;
     const bool fused = o.fused == 1 && fl && tail && dt <= D && o.pre_smooth >= 1 && o.pre_smooth <= 2 &&
                        o.post_smooth >= 1 && o.post_smooth <= 2;
@@ -311,7 +372,7 @@ struct Launcher {
       }
       for (int v = 0; v < cyc; ++v) {
         if (fused)
-          vcycle_fused<T>(*fl, dt, D, *tail, tail_smem, X, F, cmode == C_DIRECT);
+          vcycle_fused<T>(*fl, dt, D, *tail, tail_smem, X, F, cmode == C_DIRECT, rl, rfull);
         else if (hybrid)
           vcycle_hybrid<T>(lists, dt, D, *tail, tail_smem, X, F, cmode == C_DIRECT);
         else
@@ -500,7 +561,7 @@ struct Launcher {
       const bool direct32 = mixed && o.refine_passes == 1 && !o.check_residuals;
       const float* E32 = direct32 ? reinterpret_cast<const float*>(X) : nullptr;
       solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, r, sub_cmode, &lp.sub_f, lp.sub_dt, &lp.sub_tail,
-                   lp.sub_tail_smem, false, !direct32);
+                   lp.sub_tail_smem, false, !direct32, &lp.sub_r, &lp.sub_r_full);
       const double* E = mixed ? X64 : reinterpret_cast<const double*>(X);
       if (o.check_residuals) {
         cudaMemsetAsync(jobnorm, 0, P.w_jobnorm.bytes, s);
@@ -516,7 +577,7 @@ struct Launcher {
         go(F_STRIP_RHS, (32.0 + 2 * t + kfine_extra()) * stop.unk,
            [&] { launch_strip_rhs<T>(G, P.glay, a, tiles_at(stop), stop.count, X, F, X64, s); });
         solve_set<T>(lp.strip, lp.strip_coarsest, o.strip_vcycles, X, F, X64, r, strip_cmode, &lp.strip_f,
-                     lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem, false, !direct32);
+                     lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem, false, !direct32, &lp.strip_r, &lp.strip_r_full);
         if (o.check_residuals) {
           cudaMemsetAsync(jobnorm, 0, P.w_jobnorm.bytes, s);
           go(F_RESNORM, 16.0 * stop.unk,
@@ -647,7 +708,7 @@ struct Launcher {
         go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * stop.unk,
            [&] { launch_gather<T>(G, P.glay, tiles_at(stop), stop.count, X, F, X64, utbar, s); });
         solve_set<T>(lp.strip, lp.strip_coarsest, o.strip_vcycles, X, F, X64, utbar, strip_cmode, &lp.strip_f,
-                     lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem);
+                     lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem, false, true, &lp.strip_r, &lp.strip_r_full);
         LevelArgs as = a;
         as.ut = sbar;
         go(F_STRIP_UPD, 24.0 * stop.unk,
@@ -661,7 +722,7 @@ struct Launcher {
       go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * top.unk,
          [&] { launch_gather_masked<T>(G, P.glay, tiles_at(top), top.count, X, F, X64, utbar, s); });
       solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, utbar, sub_cmode, &lp.sub_f, lp.sub_dt,
-                   &lp.sub_tail, lp.sub_tail_smem, true);
+                   &lp.sub_tail, lp.sub_tail_smem, true, true, &lp.sub_r, &lp.sub_r_full);
       const size_t ebytes = (size_t)(mixed ? lp.pool64_elems : lp.pool_elems) * 8;
       cudaMemcpyAsync(tbuf, E, ebytes, cudaMemcpyDeviceToDevice, s);
       // the forward local solutions e^j, recomputed
@@ -669,7 +730,7 @@ struct Launcher {
       go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * top.unk,
          [&] { launch_gather<T>(G, P.glay, tiles_at(top), top.count, X, F, X64, r, s); });
       solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, r, sub_cmode, &lp.sub_f, lp.sub_dt, &lp.sub_tail,
-                   lp.sub_tail_smem);
+                   lp.sub_tail_smem, false, true, &lp.sub_r, &lp.sub_r_full);
       go(F_ADJ_GRAD, 32.0 * top.unk, [&] { launch_grad_local(G, P.glay, L, B, tbuf, E, use64, uin, gL, s); });
       go(F_ADJ_FIELD, 8.0 * top.unk + 8.0 * nfree, [&] { launch_rbar(G, P.glay, L, B, tbuf, use64, rbar, s); });
       const int nblk = adj_uin_blocks(P.glay, L);
@@ -723,6 +784,7 @@ int ensure_plan(mlev_ctx* ctx, const mlev_opts* o) {
   if (ctx->built_version == ctx->version && ctx->built_precision == o->precision &&
       ctx->built_tail_nodes == o->tail_nodes)
     return MLEV_OK;
+  if (fault_armed("plan_alloc")) throw std::bad_alloc();
   int rc = map_plan_error(ctx, ctx->plan.build(*o));
   if (rc) return rc;
   ctx->built_version = ctx->version;
@@ -808,17 +870,27 @@ int upload_tables(mlev_ctx* ctx, void* ws, cudaStream_t s, bool force) {
   put(P.w_subtop, P.sub_top.data(), P.sub_top.size() * sizeof(int));
   std::string terr = encode_tensor_maps(P, ws, host.data());
   if (!terr.empty()) return fail(ctx, MLEV_ECUDA, terr);
+  if (fault_armed("h2d_copy")) return cuda_fail(ctx, cudaErrorInvalidValue, "plan table copy (injected fault)");
   CK(cudaMemcpyAsync(ws, host.data(), host.size(), cudaMemcpyHostToDevice, s));
   ctx->io_h2d += (long long)host.size();
   if (!P.kappa_on_device && !P.kappa_host.empty()) {
-    CK(cudaMemcpyAsync(at<char>(ws, P.w_kstage), P.kappa_host.data(), P.kappa_host.size() * 8,
-                       cudaMemcpyHostToDevice, s));
+    const double* ksrc = P.kappa_host.data();
+    std::vector<double> knan;
+    if (fault_armed("kappa_nan")) {  // first positive value (a cell or triangle of Omega) -> NaN
+      knan = P.kappa_host;
+      for (double& v : knan)
+        if (v > 0) {
+          v = std::nan("");
+          break;
+        }
+      ksrc = knan.data();
+    }
+    CK(cudaMemcpyAsync(at<char>(ws, P.w_kstage), ksrc, P.kappa_host.size() * 8, cudaMemcpyHostToDevice, s));
     ctx->io_h2d += (long long)P.kappa_host.size() * 8;
   }
   CK(cudaStreamSynchronize(s));
   ctx->uploaded_ws = ws;
   ctx->uploaded_version = key;
-  ctx->kappa_dirty = false;
   return MLEV_OK;
 }
 
@@ -863,6 +935,8 @@ int fill_report(mlev_ctx* ctx, void* ws, cudaStream_t s, mlev_report* rep) {
     return fail(ctx, MLEV_ETIMEOUT, "a bounded device-side wait gave up (status flags " + std::to_string(flags) + ")");
   if (flags & (MLEV_ST_LEVEL1_NOCONV | MLEV_ST_RR_NOCONV | MLEV_ST_ADJ_NOCONV))
     return fail(ctx, MLEV_ENOCONV, "an iteration reached its cap (status flags " + std::to_string(flags) + ")");
+  if (flags & MLEV_ST_NONFINITE)
+    return fail(ctx, MLEV_ENOCONV, "non-finite value in the solve (status flags " + std::to_string(flags) + ")");
   if (flags) return fail(ctx, MLEV_ENOCONV, "numerical breakdown (status flags " + std::to_string(flags) + ")");
   return MLEV_OK;
 }
@@ -1002,6 +1076,7 @@ int mlev_create(mlev_ctx** out, int device) {
     mlev_ctx* c = new (std::nothrow) mlev_ctx();
     if (!c) return MLEV_ENOMEM;
     c->device = -1;
+    c->uid = g_next_ctx_uid.fetch_add(1);
     *out = c;
     return MLEV_OK;
   }
@@ -1010,6 +1085,7 @@ int mlev_create(mlev_ctx** out, int device) {
   mlev_ctx* c = new (std::nothrow) mlev_ctx();
   if (!c) return MLEV_ENOMEM;
   c->device = device;
+  c->uid = g_next_ctx_uid.fetch_add(1);
   if (cudaSetDevice(device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess) {
@@ -1031,6 +1107,7 @@ void mlev_destroy(mlev_ctx* ctx) {
 const char* mlev_last_error(const mlev_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int mlev_set_domain(mlev_ctx* ctx, int ncx, int ncy, double x0, double y0, double H, const uint8_t* cell_in) {
+  MLEV_TRY
   if (!ctx) return MLEV_EINVAL;
   if (ncx < 2 || ncy < 2 || ncx > 64 || ncy > 64 || !(H > 0) || !cell_in)
     return fail(ctx, MLEV_EINVAL, "domain: need 2 <= ncx, ncy <= 64, H > 0 and a cell mask");
@@ -1049,10 +1126,12 @@ int mlev_set_domain(mlev_ctx* ctx, int ncx, int ncy, double x0, double y0, doubl
   P.has_partition = false;
   ctx->version++;
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 int mlev_set_partition(mlev_ctx* ctx, int m, const int32_t* owner, const int32_t* overlap, double delta,
                        int glue_mode) {
+  MLEV_TRY
   if (!ctx) return MLEV_EINVAL;
   Plan& P = ctx->plan;
   if (!P.has_domain) return fail(ctx, MLEV_ESTATE, "set the domain first");
@@ -1069,9 +1148,11 @@ int mlev_set_partition(mlev_ctx* ctx, int m, const int32_t* owner, const int32_t
   P.has_partition = true;
   ctx->version++;
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 int mlev_set_levels(mlev_ctx* ctx, int n) {
+  MLEV_TRY
   if (!ctx) return MLEV_EINVAL;
   if (n < 2 || n > MLEV_MAX_LEVELS) return fail(ctx, MLEV_EINVAL, "levels: need 2 <= n <= MLEV_MAX_LEVELS");
   Plan& P = ctx->plan;
@@ -1080,9 +1161,11 @@ int mlev_set_levels(mlev_ctx* ctx, int n) {
   P.has_levels = true;
   ctx->version++;
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 int mlev_set_forms(mlev_ctx* ctx, int batch, int kappa_kind, const double* kappa, int kappa_on_device) {
+  MLEV_TRY
   if (!ctx) return MLEV_EINVAL;
   Plan& P = ctx->plan;
   if (batch < 1) return fail(ctx, MLEV_EINVAL, "batch must be >= 1");
@@ -1108,21 +1191,24 @@ int mlev_set_forms(mlev_ctx* ctx, int batch, int kappa_kind, const double* kappa
   }
   P.has_forms = true;
   ctx->version++;
-  ctx->kappa_dirty = true;
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 int mlev_workspace_size(mlev_ctx* ctx, const mlev_opts* opts, size_t* bytes) {
+  MLEV_TRY
   if (!ctx || !bytes) return MLEV_EINVAL;
   if (!opts_valid(opts)) return fail(ctx, MLEV_EINVAL, "invalid options");
   int rc = ensure_plan(ctx, opts);
   if (rc) return rc;
   *bytes = ctx->plan.ws_bytes;
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 int mlev_problem_info(mlev_ctx* ctx, long long* n_fine, long long* n_local_fine, long long* n_strip_fine,
                       int* n_coarse) {
+  MLEV_TRY
   if (!ctx) return MLEV_EINVAL;
   mlev_opts o;
   mlev_opts_default(&o);
@@ -1135,10 +1221,12 @@ int mlev_problem_info(mlev_ctx* ctx, long long* n_fine, long long* n_local_fine,
   if (n_strip_fine) *n_strip_fine = P.lp[P.n].n_strip;
   if (n_coarse) *n_coarse = P.n_coarse;
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 int mlev_solve(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
                double* lambda_out, double* u_out, mlev_report* rep) {
+  MLEV_TRY
   int rc = prepare(ctx, opts, workspace, ws_bytes);
   if (rc) return rc;
   if (!lambda_out) return fail(ctx, MLEV_EINVAL, "lambda_out is required");
@@ -1150,10 +1238,12 @@ int mlev_solve(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_
   if (rc) return rc;
   if (rep) return fill_report(ctx, workspace, s, rep);
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 int mlev_solve_host(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
                     const double* kappa_host, double* lambda_host, double* u_host, mlev_report* rep) {
+  MLEV_TRY
   int rc = prepare(ctx, opts, workspace, ws_bytes);
   if (rc) return rc;
   if (!lambda_host) return fail(ctx, MLEV_EINVAL, "lambda_host is required");
@@ -1182,19 +1272,23 @@ int mlev_solve_host(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_
   CK(cudaStreamSynchronize(s));
   if (rep) return fill_report(ctx, workspace, s, rep);
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 int mlev_grad_workspace_size(mlev_ctx* ctx, const mlev_opts* opts, size_t* bytes) {
+  MLEV_TRY
   if (!ctx || !bytes) return MLEV_EINVAL;
   if (!opts_valid(opts)) return fail(ctx, MLEV_EINVAL, "invalid options");
   int rc = ensure_plan(ctx, opts);
   if (rc) return rc;
   *bytes = ctx->plan.ws_grad_bytes;
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 int mlev_grad_kappa(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_t ws_bytes, void* stream,
                     const double* dlambda, int layout, double* dkappa, double* lambda_out, mlev_report* rep) {
+  MLEV_TRY
   int rc = prepare(ctx, opts, workspace, ws_bytes);
   if (rc) return rc;
   const Plan& P = ctx->plan;
@@ -1212,11 +1306,13 @@ int mlev_grad_kappa(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_
   if (rc) return rc;
   if (rep) return fill_report(ctx, workspace, s, rep);
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 }  // extern "C"
 
 extern "C" int mlev_profile_read(mlev_ctx* ctx, mlev_kernel_stat* out, int capacity, int* count) {
+  MLEV_TRY
   if (!ctx) return MLEV_EINVAL;
   if (!ctx->prof_valid) return fail(ctx, MLEV_ESTATE, "no profiled solve has completed");
   if (count) *count = F_COUNT;
@@ -1228,6 +1324,7 @@ extern "C" int mlev_profile_read(mlev_ctx* ctx, mlev_kernel_stat* out, int capac
     out[i].bytes = ctx->prof[i].bytes;
   }
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }
 
 // ---------------------------------------------------------------------------------
@@ -1239,10 +1336,15 @@ static __device__ __align__(256) unsigned char g_noalloc_workspace[MLEV_NOALLOC_
 namespace {
 std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[256] = {nullptr};
+// whose plan tables the array of each device holds: context uid and plan generation
+// (0 = none yet); a context that finds its own tables there skips the copy
+unsigned long long g_noalloc_owner[256] = {0};
+long long g_noalloc_gen[256] = {0};
 }  // namespace
 
 extern "C" int mlev_solve_noalloc(mlev_ctx* ctx, const mlev_opts* opts, void* stream, double* lambda_out,
                                   double* u_out, mlev_report* rep) {
+  MLEV_TRY
   if (!ctx) return MLEV_EINVAL;
   if (ctx->device < 0) return fail(ctx, MLEV_ESTATE, "planning-only context (device -1) cannot solve");
   if (ctx->device >= 256) return fail(ctx, MLEV_EUNSUPPORTED, "device index above 255");
@@ -1270,10 +1372,22 @@ extern "C" int mlev_solve_noalloc(mlev_ctx* ctx, const mlev_opts* opts, void* st
   if (rc) return rc;
   if (!lambda_out) return fail(ctx, MLEV_EINVAL, "lambda_out is required");
   cudaStream_t s = (cudaStream_t)stream;
-  rc = upload_tables(ctx, ws, s, true);  // the array is shared: always bring this problem's tables
-  if (rc) return rc;
+  {
+    // the array is shared by every context: copy this problem's tables (and staged kappa) in
+    // unless the last copy into it was this context's, for its current plan
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    const bool mine = g_noalloc_owner[ctx->device] == ctx->uid && g_noalloc_gen[ctx->device] == ctx->plan_gen;
+    if (!mine) {
+      g_noalloc_owner[ctx->device] = 0;  // stays unowned if the copy fails
+      rc = upload_tables(ctx, ws, s, true);
+      if (rc) return rc;
+      g_noalloc_owner[ctx->device] = ctx->uid;
+      g_noalloc_gen[ctx->device] = ctx->plan_gen;
+    }
+  }
   rc = solve_impl(ctx, opts, ws, MLEV_NOALLOC_WORKSPACE_BYTES, s, kappa_device_src(ctx, ws), lambda_out, u_out);
   if (rc) return rc;
   if (rep) return fill_report(ctx, ws, s, rep);
   return MLEV_OK;
+  MLEV_CATCH(ctx)
 }

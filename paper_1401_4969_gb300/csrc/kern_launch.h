@@ -51,6 +51,16 @@ template <typename T>
 void launch_mg_tail(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, const T* inv, int nd_max, int nlev,
                     int pre, int post, int csweeps, double omega, int load_x, size_t smem, cudaStream_t s);
 
+// ---- register-blocked fused multigrid, FP32 (kern_mgreg.cu); tiles of MLEV_RTILE_W x
+// MLEV_RTILE_H nodes; full = every grid of the tile list has no region mask ----
+bool rkernels_support(int kappa_kind, int pre, int post);
+// down: nu sweeps on depth d (x read from X, smoothed x written to XS), residual, restriction to
+// depth d + 1 (f and x = 0 there, in F and X)
+void launch_rdown(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F, int nu,
+                  double omega, int black_zero, cudaStream_t s);
+// up: x = XS + P x_c (x_c from X at depth d + 1), nu sweeps, written to X
+void launch_rup(const DevGeom& G, const Tile* tiles, int n, int full, const float* XS, float* X, const float* F, int nu,
+                double omega, int red_only, cudaStream_t s);
 // ---- global fields (kern_field.cu) ----
 struct LevelArgs {
   int L;                 // current level

@@ -1,0 +1,359 @@
+// Register-blocked fused multigrid kernels (FP32) for the masked SPD problems of
+// Algorithm 4.1: the auxiliary problems on Omega_j (Eq. Aux_Problem) and the G_{m+1}
+// problem (Eq. G_m+1_Problem). Same operations as k_mg_down / k_mg_up (kern_mgfused.cu)
+// -- red-black Gauss-Seidel sweeps, residual, restriction P^T r, prolongation x += P x_c
+// -- with the grid values held in registers instead of shared memory:
+//
+// * A block of 8 warps covers a 128 x 64 box of one grid; warp w holds rows 8w .. 8w+7 of
+//   the box and lane l holds columns 4l .. 4l+3 of every one of those rows (x and f as
+//   float4 loads straight from the pools), so a half-sweep reads the north / south
+//   neighbours from the thread's own registers, the west / east neighbour across a lane
+//   boundary by one warp shuffle per row, and the rows across warp boundaries from a small
+//   shared-memory exchange (one barrier per half-sweep).
+// * Temporal blocking as in the shared-memory kernels: every half-sweep invalidates one more
+//   ring of the box, so the box carries a halo of 8 columns (float4-aligned) and 6 rows
+//   around its 112 x 52 output tile (2 NU + 2 <= 6 for NU <= 2).
+// * The down kernel reads x from X and writes the smoothed x to the separate pool XS (the
+//   up kernel reads XS and writes X): a box never reads values another block of the same
+//   launch writes, so results do not depend on the order in which blocks run.
+//
+// Node (i, j) of the box has colour (i + j) & 1 (0 red, 1 black) in its grid's coordinates;
+// the box origin is even in both directions, so the colour of register (q, k) (row q,
+// column k) is (q + k) & 1 and every register index below is known at compile time.
+#include "kern_launch.h"
+
+namespace mlev {
+
+namespace {
+
+constexpr int kRW = 128;             // box width (nodes)
+constexpr int kRR = 8;               // rows per warp
+constexpr int kRWarps = 8;           // warps per block
+constexpr int kRHX = 8;              // halo columns on each side
+constexpr int kRHY = 6;              // halo rows on each side
+constexpr int kROW = kRW - 2 * kRHX; // 112 output columns
+constexpr int kROH = kRR * kRWarps - 2 * kRHY;  // 52 output rows
+static_assert(kROW == MLEV_RTILE_W && kROH == MLEV_RTILE_H, "tile size of the planner");
+
+struct RegTile {
+  float v[kRR][4];
+};
+
+// Coefficient weights of the stiffness row of node (gi, gj) (global lattice of level l).
+template <int KK>
+__device__ __forceinline__ EW<float> rweights(const KappaDev& kv, int p, int l, int gi, int gj) {
+  return edge_weights_t<float, KK>(kv, p, l, gi, gj);
+}
+
+// Row exchange between the warps of the block: buf[0][w] = first row of warp w, buf[1][w] =
+// its last row. After the barrier warp w reads the row below its first (last row of warp
+// w-1) and the row above its last (first row of warp w+1); the outermost warps read zeros
+// (the box's outer ring, which no output depends on).
+__device__ __forceinline__ void exchange_rows(float4 (*buf)[kRWarps][32], const RegTile& a, float (&below)[4],
+                                              float (&above)[4], int w, int lane) {
+  buf[0][w][lane] = make_float4(a.v[0][0], a.v[0][1], a.v[0][2], a.v[0][3]);
+  buf[1][w][lane] = make_float4(a.v[kRR - 1][0], a.v[kRR - 1][1], a.v[kRR - 1][2], a.v[kRR - 1][3]);
+  __syncthreads();
+  const float4 b = w > 0 ? buf[1][w - 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 t = w < kRWarps - 1 ? buf[0][w + 1][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  below[0] = b.x; below[1] = b.y; below[2] = b.z; below[3] = b.w;
+  above[0] = t.x; above[1] = t.y; above[2] = t.z; above[3] = t.w;
+}
+
+// One red-black half-sweep of colour C over the thread's registers (C, the row parity and
+// the column are compile-time, so each row updates columns k0 and k0 + 2 with one shuffle).
+template <int KK, int C>
+__device__ __forceinline__ void rhalf_sweep(RegTile& x, const RegTile& f, unsigned mask, const float (&below)[4],
+                                            const float (&above)[4], const KappaDev& kv, int p, int l, int gi0,
+                                            int gj0, float omega) {
+#pragma unroll
+  for (int q = 0; q < kRR; ++q) {
+    const int k0 = (C ^ q) & 1;
+    // the row updates columns k0 and k0 + 2: column 0 needs the west neighbour from lane - 1,
+    // column 3 the east neighbour from lane + 1 (one shuffle either way)
+    float nb;
+    if (k0 == 0) nb = __shfl_up_sync(0xffffffffu, x.v[q][3], 1);
+    else nb = __shfl_down_sync(0xffffffffu, x.v[q][0], 1);
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const int k = k0 + 2 * kk;
+      const float xw = k == 0 ? nb : x.v[q][k == 0 ? 0 : k - 1];
+      const float xe = k == 3 ? nb : x.v[q][k == 3 ? 3 : k + 1];
+      const float xs = q == 0 ? below[k] : x.v[q == 0 ? 0 : q - 1][k];
+      const float xn = q == kRR - 1 ? above[k] : x.v[q == kRR - 1 ? kRR - 1 : q + 1][k];
+      float nv;
+      if (KK == MLEV_KAPPA_ONE) {
+        const float s = f.v[q][k] + xe + xw + xn + xs;
+        nv = x.v[q][k] + omega * (s / 4.0f - x.v[q][k]);
+      } else {
+        const EW<float> w = rweights<KK>(kv, p, l, gi0 + k, gj0 + q);
+        const float s = f.v[q][k] + w.e * xe + w.w * xw + w.n * xn + w.s * xs;
+        nv = x.v[q][k] + omega * (s / (w.e + w.w + w.n + w.s) - x.v[q][k]);
+      }
+      if (mask & (1u << (q * 4 + k))) x.v[q][k] = nv;
+    }
+  }
+}
+
+// Loads rows [r0, r0 + 8) x columns [c0, c0 + 4) of a pitched grid array (zeros outside the
+// grid rows / the pitched row).
+__device__ __forceinline__ void rload(RegTile& t, const float* base, int pitch, int ny, int c0, int r0) {
+  const bool colok = c0 >= 0 && c0 + 3 < pitch;
+#pragma unroll
+  for (int q = 0; q < kRR; ++q) {
+    const int j = r0 + q;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (colok && j >= 0 && j <= ny) v = __ldg(reinterpret_cast<const float4*>(base + (long long)j * pitch + c0));
+    t.v[q][0] = v.x; t.v[q][1] = v.y; t.v[q][2] = v.z; t.v[q][3] = v.w;
+  }
+}
+
+// Unknown mask of the thread's 8 x 4 nodes: bit q * 4 + k.
+template <bool FULL>
+__device__ __forceinline__ unsigned rmask(const DevGeom& G, const GridDesc& g, int c0, int r0) {
+  unsigned m = 0;
+#pragma unroll
+  for (int q = 0; q < kRR; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = c0 + k, j = r0 + q;
+      bool u;
+      if (FULL) u = i >= 1 && j >= 1 && i < g.nx && j < g.ny;
+      else u = is_unknown(G, g, i, j);
+      if (u) m |= 1u << (q * 4 + k);
+    }
+  return m;
+}
+
+// Writes the thread's rows that lie in the output tile [x0, x0 + 112) x [y0, y0 + 52) of
+// the grid (the columns of lanes 2 .. 29).
+__device__ __forceinline__ void rstore(const RegTile& t, float* base, int pitch, int ny, int c0, int r0, int y0,
+                                       int lane) {
+  if (lane < 2 || lane >= 30 || c0 + 3 >= pitch) return;
+#pragma unroll
+  for (int q = 0; q < kRR; ++q) {
+    const int j = r0 + q;
+    if (j < y0 || j >= y0 + kROH || j > ny) continue;
+    *reinterpret_cast<float4*>(base + (long long)j * pitch + c0) = make_float4(t.v[q][0], t.v[q][1], t.v[q][2], t.v[q][3]);
+  }
+}
+
+struct RGrid {  // the fields of a GridDesc the kernels use, read once
+  int nx, ny, pitch, ox, oy, level, problem;
+  long long off;
+};
+__device__ __forceinline__ RGrid rgrid(const GridDesc& g) {
+  return RGrid{g.nx, g.ny, g.pitch, g.ox, g.oy, g.level, g.problem, g.off};
+}
+
+}  // namespace
+
+// Down leg on one tile: NU red-black sweeps (red first), the residual, and its restriction
+// to the next coarser grid (f_c = P^T r, x_c = 0) for the coarse nodes of the tile.
+template <int KK, int NU, bool FULL>
+__global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restrict__ tiles, const float* __restrict__ X,
+                                                  float* XC, float* __restrict__ XS, float* F, float omega,
+                                                  int black_zero) {
+  __shared__ float4 xbuf[2][2][kRWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const Tile t = tiles[blockIdx.x];
+  const GridDesc& gd = G.grids[t.grid];
+  const RGrid g = rgrid(gd);
+  const GridDesc& gcd = G.grids[t.grid + 1];
+  const RGrid gc = rgrid(gcd);
+  const int c0 = t.x0 - kRHX + 4 * lane, r0 = t.y0 - kRHY + kRR * w;
+  RegTile x, f;
+  rload(x, X + g.off, g.pitch, g.ny, c0, r0);
+  rload(f, F + g.off, g.pitch, g.ny, c0, r0);
+  const unsigned mask = rmask<FULL>(G, gd, c0, r0);
+#pragma unroll
+  for (int q = 0; q < kRR; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (!(mask & (1u << (q * 4 + k)))) x.v[q][k] = 0.f;
+  const int gi0 = g.ox + c0, gj0 = g.oy + r0;
+  float below[4], above[4];
+#pragma unroll
+  for (int s = 0; s < NU; ++s) {
+    exchange_rows(xbuf[0], x, below, above, w, lane);
+    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0, omega);
+    exchange_rows(xbuf[1], x, below, above, w, lane);
+    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0, omega);
+  }
+  rstore(x, XS + g.off, g.pitch, g.ny, c0, r0, t.y0, lane);
+  // residual r = f - A x in f's registers (0 off the unknowns); with black_zero only the red
+  // nodes (the black residuals vanish after the closing black half-sweep)
+  exchange_rows(xbuf[0], x, below, above, w, lane);
+#pragma unroll
+  for (int q = 0; q < kRR; ++q) {
+    const float wx = __shfl_up_sync(0xffffffffu, x.v[q][3], 1);
+    const float ex = __shfl_down_sync(0xffffffffu, x.v[q][0], 1);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float xw = k == 0 ? wx : x.v[q][k == 0 ? 0 : k - 1];
+      const float xe = k == 3 ? ex : x.v[q][k == 3 ? 3 : k + 1];
+      const float xs = q == 0 ? below[k] : x.v[q == 0 ? 0 : q - 1][k];
+      const float xn = q == kRR - 1 ? above[k] : x.v[q == kRR - 1 ? kRR - 1 : q + 1][k];
+      float r;
+      if (KK == MLEV_KAPPA_ONE) {
+        r = f.v[q][k] - (4.0f * x.v[q][k] - xe - xw - xn - xs);
+      } else {
+        const EW<float> wt = rweights<KK>(G.kap, g.problem, g.level, gi0 + k, gj0 + q);
+        r = f.v[q][k] - ((wt.e + wt.w + wt.n + wt.s) * x.v[q][k] - wt.e * xe - wt.w * xw - wt.n * xn - wt.s * xs);
+      }
+      const bool skip = black_zero && ((q + k) & 1);
+      f.v[q][k] = (!skip && (mask & (1u << (q * 4 + k)))) ? r : 0.f;
+    }
+  }
+  // restriction: coarse node (I, J) = fine (2I, 2J) = register (q, k), q even, k in {0, 2};
+  // needs r of the row below the warp (its q = -1) and of the column left of the lane
+  exchange_rows(xbuf[1], f, below, above, w, lane);
+  const bool out_col = lane >= 2 && lane < 30;
+#pragma unroll
+  for (int q = 0; q < kRR; q += 2) {
+    const float wr0 = __shfl_up_sync(0xffffffffu, f.v[q][3], 1);  // r(q, -1)
+    const float wrm = __shfl_up_sync(0xffffffffu, q == 0 ? below[3] : f.v[q == 0 ? 0 : q - 1][3], 1);  // r(q-1, -1)
+    const int j = r0 + q;
+    if (!out_col || j < t.y0 || j >= t.y0 + kROH) continue;
+    const int J = j >> 1;
+    if (J > gc.ny) continue;
+    float val[2];
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const int k = 2 * kk;
+      const float rc = f.v[q][k];
+      const float rne = f.v[q + 1][k + 1];
+      const float rsw = k == 0 ? wrm : (q == 0 ? below[k - 1 < 0 ? 0 : k - 1] : f.v[q == 0 ? 0 : q - 1][k - 1 < 0 ? 0 : k - 1]);
+      float half = rne + rsw;
+      if (!black_zero) {
+        const float re = f.v[q][k + 1];
+        const float rw = k == 0 ? wr0 : f.v[q][k - 1 < 0 ? 0 : k - 1];
+        const float rn = f.v[q + 1][k];
+        const float rs = q == 0 ? below[k] : f.v[q == 0 ? 0 : q - 1][k];
+        half += re + rw + rn + rs;
+      }
+      val[kk] = rc + 0.5f * half;
+    }
+    const int I = c0 >> 1;
+    float* fr = F + gc.off + (long long)J * gc.pitch;
+    float* xr = XC + gc.off + (long long)J * gc.pitch;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const int Ik = I + kk;
+      if (Ik > gc.nx) continue;
+      const bool u = FULL ? (Ik >= 1 && J >= 1 && Ik < gc.nx && J < gc.ny) : is_unknown(G, gcd, Ik, J);
+      fr[Ik] = u ? val[kk] : 0.f;
+      xr[Ik] = 0.f;
+    }
+  }
+}
+
+// Up leg on one tile: x += P x_c (the coarse correction, from X on the coarser grid; with
+// red_only only the red nodes, since a plain Gauss-Seidel black half-sweep opens the
+// post-smoothing), then NU red-black sweeps (black first). Reads x from XS, writes X.
+template <int KK, int NU, bool FULL>
+__global__ void __launch_bounds__(256, 2) k_rup(DevGeom G, const Tile* __restrict__ tiles, const float* __restrict__ XS,
+                                                float* X, const float* __restrict__ F, float omega, int red_only) {
+  __shared__ float4 xbuf[2][2][kRWarps][32];
+  __shared__ float xc[34][66];  // coarse nodes [by0/2, by0/2 + 33] x [bx0/2, bx0/2 + 65]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const Tile t = tiles[blockIdx.x];
+  const GridDesc& gd = G.grids[t.grid];
+  const RGrid g = rgrid(gd);
+  const RGrid gc = rgrid(G.grids[t.grid + 1]);
+  const int bx0 = t.x0 - kRHX, by0 = t.y0 - kRHY;
+  const int c0 = bx0 + 4 * lane, r0 = by0 + kRR * w;
+  // coarse correction values of the box (0 outside the coarse grid)
+  {
+    const int CX0 = bx0 >> 1, CY0 = by0 >> 1;  // both even, so exact halves
+    for (int e = threadIdx.x; e < 34 * 66; e += blockDim.x) {
+      const int jj = e / 66, ii = e - jj * 66;
+      const int I = CX0 + ii, J = CY0 + jj;
+      float v = 0.f;
+      if (I >= 0 && J >= 0 && I <= gc.nx && J <= gc.ny) v = X[gc.off + (long long)J * gc.pitch + I];
+      xc[jj][ii] = v;
+    }
+  }
+  RegTile x, f;
+  rload(x, XS + g.off, g.pitch, g.ny, c0, r0);
+  rload(f, F + g.off, g.pitch, g.ny, c0, r0);
+  const unsigned mask = rmask<FULL>(G, gd, c0, r0);
+  __syncthreads();
+  // prolongation (exact P1 interpolation on the SW-NE mesh)
+#pragma unroll
+  for (int q = 0; q < kRR; ++q)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int bit = q * 4 + k;
+      if (!(mask & (1u << bit))) {
+        x.v[q][k] = 0.f;
+        continue;
+      }
+      if (red_only && ((q + k) & 1)) continue;
+      const int ci = 2 * lane + (k >> 1), cj = 4 * w + (q >> 1);  // coarse node (i >> 1, j >> 1) in xc
+      float v;
+      if (!(k & 1) && !(q & 1)) v = xc[cj][ci];
+      else if ((k & 1) && !(q & 1)) v = 0.5f * (xc[cj][ci] + xc[cj][ci + 1]);
+      else if (!(k & 1) && (q & 1)) v = 0.5f * (xc[cj][ci] + xc[cj + 1][ci]);
+      else v = 0.5f * (xc[cj][ci] + xc[cj + 1][ci + 1]);
+      x.v[q][k] += v;
+    }
+  const int gi0 = g.ox + c0, gj0 = g.oy + r0;
+  float below[4], above[4];
+#pragma unroll
+  for (int s = 0; s < NU; ++s) {  // two exchange buffers in turn: one barrier per half-sweep
+    exchange_rows(xbuf[0], x, below, above, w, lane);
+    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0, omega);
+    exchange_rows(xbuf[1], x, below, above, w, lane);
+    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0, omega);
+  }
+  rstore(x, X + g.off, g.pitch, g.ny, c0, r0, t.y0, lane);
+}
+
+// ------------------------------------------------------------------ launchers
+bool rkernels_support(int kappa_kind, int pre, int post) {
+  return (kappa_kind == MLEV_KAPPA_ONE || kappa_kind == MLEV_KAPPA_PER_COARSE_CELL) && pre >= 1 && pre <= 2 &&
+         post >= 1 && post <= 2;
+}
+
+template <int KK, int NU>
+static void rdown_kk(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F,
+                     double omega, int black_zero, cudaStream_t s) {
+  if (full)
+    k_rdown<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, X, X, XS, F, (float)omega, black_zero);
+  else
+    k_rdown<KK, NU, false><<<n, 256, 0, s>>>(G, tiles, X, X, XS, F, (float)omega, black_zero);
+}
+template <int KK, int NU>
+static void rup_kk(const DevGeom& G, const Tile* tiles, int n, int full, const float* XS, float* X, const float* F,
+                   double omega, int red_only, cudaStream_t s) {
+  if (full)
+    k_rup<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, XS, X, F, (float)omega, red_only);
+  else
+    k_rup<KK, NU, false><<<n, 256, 0, s>>>(G, tiles, XS, X, F, (float)omega, red_only);
+}
+
+void launch_rdown(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F, int nu,
+                  double omega, int black_zero, cudaStream_t s) {
+  if (!n) return;
+  if (G.kap.kind == MLEV_KAPPA_ONE) {
+    if (nu == 1) rdown_kk<MLEV_KAPPA_ONE, 1>(G, tiles, n, full, X, XS, F, omega, black_zero, s);
+    else rdown_kk<MLEV_KAPPA_ONE, 2>(G, tiles, n, full, X, XS, F, omega, black_zero, s);
+  } else {
+    if (nu == 1) rdown_kk<MLEV_KAPPA_PER_COARSE_CELL, 1>(G, tiles, n, full, X, XS, F, omega, black_zero, s);
+    else rdown_kk<MLEV_KAPPA_PER_COARSE_CELL, 2>(G, tiles, n, full, X, XS, F, omega, black_zero, s);
+  }
+}
+void launch_rup(const DevGeom& G, const Tile* tiles, int n, int full, const float* XS, float* X, const float* F, int nu,
+                double omega, int red_only, cudaStream_t s) {
+  if (!n) return;
+  if (G.kap.kind == MLEV_KAPPA_ONE) {
+    if (nu == 1) rup_kk<MLEV_KAPPA_ONE, 1>(G, tiles, n, full, XS, X, F, omega, red_only, s);
+    else rup_kk<MLEV_KAPPA_ONE, 2>(G, tiles, n, full, XS, X, F, omega, red_only, s);
+  } else {
+    if (nu == 1) rup_kk<MLEV_KAPPA_PER_COARSE_CELL, 1>(G, tiles, n, full, XS, X, F, omega, red_only, s);
+    else rup_kk<MLEV_KAPPA_PER_COARSE_CELL, 2>(G, tiles, n, full, XS, X, F, omega, red_only, s);
+  }
+}
+
+}  // namespace mlev

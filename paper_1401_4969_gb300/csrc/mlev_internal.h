@@ -44,6 +44,11 @@ struct GridDesc {
 #define MLEV_TMA_COY 3
 #define MLEV_TMAP_BYTES 128
 
+// Output tile of the register-blocked fused multigrid kernels (kern_mgreg.cu): 112 x 52
+// nodes, origins multiples of the tile size (even, and x a multiple of 4 for float4 rows).
+#define MLEV_RTILE_W 112
+#define MLEV_RTILE_H 52
+
 struct Tile {  // a block of nodes of one grid: origin (x0, y0), size fixed by the kernel
   int grid;
   int x0, y0;

@@ -386,7 +386,8 @@ std::string Plan::build(const mlev_opts& o) {
       return (size_t)(2 * tot + extra) * tsize + (size_t)tot;  // x, f, dense-solve buffer, unknown mask
     };
     auto plan_fused = [&](const std::vector<std::vector<int>>& by_depth, std::vector<TileList>& fl, int& dt,
-                          TileList& tail, size_t& tail_smem, int extra) {
+                          TileList& tail, size_t& tail_smem, int extra, std::vector<TileList>& rl,
+                          std::vector<int>& rfull) {
       const int D = (int)by_depth.size() - 1;
       dt = D + 1;
       tail_smem = 0;
@@ -417,6 +418,20 @@ std::string Plan::build(const mlev_opts& o) {
         }
         fl[d].count = (int)((long long)tiles.size() - fl[d].off);
       }
+      rl.assign(fl.size(), TileList());
+      rfull.assign(fl.size(), 1);
+      for (int d = 0; d < (int)rl.size(); ++d) {
+        rl[d].off = (long long)tiles.size();
+        for (int gi : by_depth[d]) {
+          const GridDesc& g = grids[gi];
+          rfull[d] = rfull[d] && g.full;
+          for (int y = 0; y <= g.ny; y += MLEV_RTILE_H)
+            for (int x = 0; x <= g.nx; x += MLEV_RTILE_W)
+              if (block_has_unknown(*this, g, x, y, MLEV_RTILE_W, MLEV_RTILE_H)) tiles.push_back(Tile{gi, x, y});
+          rl[d].unk += unk_of(gi);
+        }
+        rl[d].count = (int)((long long)tiles.size() - rl[d].off);
+      }
       if (dt <= D) {
         tail.off = (long long)tiles.size();
         for (int gi : by_depth[dt]) {
@@ -426,8 +441,10 @@ std::string Plan::build(const mlev_opts& o) {
         tail.count = (int)by_depth[dt].size();
       }
     };
-    plan_fused(sub_by_depth, P.sub_f, P.sub_dt, P.sub_tail, P.sub_tail_smem, sub_direct ? nd_max : 0);
-    plan_fused(strip_by_depth, P.strip_f, P.strip_dt, P.strip_tail, P.strip_tail_smem, 0);
+    plan_fused(sub_by_depth, P.sub_f, P.sub_dt, P.sub_tail, P.sub_tail_smem, sub_direct ? nd_max : 0, P.sub_r,
+               P.sub_r_full);
+    plan_fused(strip_by_depth, P.strip_f, P.strip_dt, P.strip_tail, P.strip_tail_smem, 0, P.strip_r,
+               P.strip_r_full);
     // TMA tensor maps for every grid a fused down / up kernel reads (depths 0 .. dt)
     auto give_maps = [&](const std::vector<std::vector<int>>& by_depth, int dt) {
       if (dt == 0) return;
@@ -535,6 +552,7 @@ std::string Plan::build(const mlev_opts& o) {
   take(w_x, (size_t)pmax * tsize);
   take(w_f, (size_t)pmax * tsize);
   take(w_x64, (size_t)p64max * 8);
+  take(w_xs, tsize == 4 ? (size_t)pmax * 4 : 0);
   take(w_aug, (size_t)B * ncx * ncy * 12 * 8);
   take(w_lam, (size_t)B * (n + 1) * 8);
   take(w_c, (size_t)B * (ncx + 1) * (ncy + 1) * 8);

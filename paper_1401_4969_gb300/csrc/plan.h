@@ -42,6 +42,10 @@ struct LevelPlan {                      // correction level L = k + 1
   int sub_dt = 0, strip_dt = 0;          // first tail depth (= number of depths + 1 if no tail fits)
   TileList sub_tail, strip_tail;
   size_t sub_tail_smem = 0, strip_tail_smem = 0;
+  // register-blocked fused kernels: MLEV_RTILE_W x MLEV_RTILE_H tiles (only tiles with
+  // unknowns) of the depths above the tail, and whether every grid of a depth is full
+  std::vector<TileList> sub_r, strip_r;
+  std::vector<int> sub_r_full, strip_r_full;
 };
 
 constexpr int kDirectMax = 128;         // largest coarsest window solved with a dense inverse
@@ -95,6 +99,7 @@ struct Plan {
   Span w_kstage, w_klvl, w_klvl_f, w_kcf, w_band, w_ut[2], w_uin, w_r, w_l1vec, w_l1pool[2];
   Span w_x, w_f, w_x64, w_aug, w_lam, w_c, w_c0, w_stat, w_jobnorm, w_chol, w_out_lam, w_out_u, w_cinv, w_tmaps;
   Span w_rrpre;  // Rayleigh-Ritz factors prepared ahead of a level (mixed precision only)
+  Span w_xs;     // smoothed x of the register-blocked down kernels (FP32, same layout as w_x)
   size_t ws_bytes = 0;
   size_t tables_bytes = 0;
   // adjoint (mlev_grad_kappa): extra regions after the solve's, up to ws_grad_bytes

@@ -43,6 +43,34 @@ def test_noalloc_matches_workspace_entry_point_twice(make):
     s.close()
 
 
+@pytest.mark.parametrize("graph", [0, 1])
+def test_noalloc_contexts_take_turns_on_the_shared_array(graph):
+    """Two contexts with different problems alternate on the one array (A, B, A, B): each
+    call must bring its own plan tables back in, whether the solve is replayed from a
+    graph or launched directly, and match mlev_solve on a workspace of its own."""
+    from paper_1401_4969_gb300 import mlev
+
+    probs = {"A": W.config1(), "B": W.kappa_coarse_batch(W.unit_square(8, 4, 3, overlap=1), batch=3, seed=11)}
+    solvers = {k: mlev.Solver(p) for k, p in probs.items()}
+    o = mlev.default_opts(use_graph=graph)
+    ref = {}
+    for k, s in solvers.items():
+        lam, u, _ = s.solve(mlev.default_opts(), want_u=True)
+        ref[k] = (lam.cpu().numpy(), u.cpu().numpy())
+    for k in ("A", "B", "A", "B", "A"):
+        s, p = solvers[k], probs[k]
+        lam, u = s.alloc_outputs(want_u=True)
+        s.solve_noalloc(o, lam, u)
+        rep = s.solve_noalloc(o, lam, u, report=True)  # a warm call right after: no table copy
+        assert rep["status_flags"] == 0 and rep["h2d_bytes"] == 0, (k, rep["h2d_bytes"])
+        lam, u = lam.cpu().numpy(), u.cpu().numpy()
+        for b in range(p.batch):
+            assert abs(lam[b] - ref[k][0][b]) <= 1e-8 * abs(ref[k][0][b]), (k, b)
+            assert _b_norm(p, u[b] - ref[k][1][b]) <= 1e-6, (k, b)
+    for s in solvers.values():
+        s.close()
+
+
 def test_noalloc_rejects_problems_above_its_limit():
     from paper_1401_4969_gb300 import mlev
 
