@@ -17,7 +17,11 @@ eigenvalue problem") computes:
 * ``partition`` - D_j, Omega_j, G_j and G_{m+1} (Section 4, before Algorithm 4.1);
 * ``multilevel``- Algorithm 4.2 (level-1 eigenproblem, then Correction steps),
                   Algorithm 4.1 (auxiliary local problems, gluing with the
-                  G_{m+1} problem, Rayleigh-Ritz on V_{0H} + span{u~}).
+                  G_{m+1} problem, Rayleigh-Ritz on V_{0H} + span{u~});
+* ``multiple``  - the same for the q smallest eigenpairs (the subspace form: one
+                  correction per eigenpair, one Rayleigh-Ritz on
+                  V_{0H} + span{u~_1 .. u~_q}; Section 4's multiple-eigenvalue remark,
+                  Table 1).
 
 Everything is float64, with sparse direct solves (``scipy.sparse.linalg.splu``)
 and dense generalized symmetric eigensolves (``scipy.linalg.eigh``).

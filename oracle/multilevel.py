@@ -110,39 +110,28 @@ class StepTrace:
     coeff: np.ndarray
 
 
-def correction(hier: Hierarchy, k: int, lam_k: float, u_k: np.ndarray, trace: bool = False):
+def local_solve(args):
+    """One auxiliary problem of step 1: the sparse direct solve A_j e = rhs_j (a top-level
+    function, so a process pool can run the m independent solves of a level)."""
+    A, rhs = args
+    return spla.splu(A).solve(rhs)
+
+
+def correction(hier: Hierarchy, k: int, lam_k: float, u_k: np.ndarray, trace: bool = False, mapper=map):
     """Algorithm 4.1: (lambda_{h_{k+1}}, u_{h_{k+1}}) = Correction(V_{0H}, lambda_{h_k}, u_{h_k}, V_{0h_{k+1}}).
 
     u_k is the full nodal vector on level k (zero on dOmega); returns the level-(k+1) pair.
+    `mapper(fn, items)` runs the m independent local solves of step 1 (the built-in map by
+    default; a process pool's map gives the paper's one-processor-per-subdomain model).
     """
     u = hier.interp[k] @ u_k                      # u_{h_k} as an element of V_{h_{k+1}} (exact embedding)
-    return correction_on_level(hier, k + 1, lam_k, u, trace)
+    return correction_on_level(hier, k + 1, lam_k, u, trace, mapper)
 
 
-def correction_on_level(hier: Hierarchy, L: int, lam_k: float, u: np.ndarray, trace: bool = False):
+def correction_on_level(hier: Hierarchy, L: int, lam_k: float, u: np.ndarray, trace: bool = False, mapper=map):
     """Steps 1-3 of Algorithm 4.1 on level L for a given pair (lambda_{h_k}, u_{h_k}) already in V_{h_L}."""
     K, M = hier.K[L], hier.M[L]
-    part: LevelPartition = hier.parts[L]
-    Mu = M @ u
-    Ku = K @ u
-    # Step 1 (Eq. Aux_Problem): a(e^j, v) = lambda_k b(u_k, v) - a(u_k, v) for v in V_{0h_{k+1}}(Omega_j)
-    rhs = lam_k * Mu - Ku
-    u_tilde_j, e_list = [], []
-    for loc in part.local:
-        A = K[loc][:, loc].tocsc()
-        e = np.zeros_like(u)
-        e[loc] = spla.splu(A).solve(rhs[loc])
-        e_list.append(e)
-        u_tilde_j.append(u + e)                    # u~^j = u_{h_k} + e^j on Omega_j
-    # Step 2: u~ = u~^j on closed G_j, and on G_{m+1} solve Eq. G_m+1_Problem with Dirichlet data u~^j.
-    ut = np.zeros_like(u)
-    for j, g in enumerate(part.g_nodes):
-        ut[g] = u_tilde_j[j][g]
-    S = part.strip
-    if S.size:
-        # a(u~^{m+1}, v) = lambda_k b(u_k, v), v in V_{0h}(G_{m+1}); known values of u~ move to the right.
-        rhs_s = lam_k * Mu[S] - (K[S] @ ut)        # ut is zero on S here
-        ut[S] = spla.splu(K[S][:, S].tocsc()).solve(rhs_s)
+    ut, e_list = glued(hier, L, lam_k, u, mapper)
     # Step 3 (Eq. Eigen_Augment_Problem): Rayleigh-Ritz on V_{0H} + span{u~}.
     f = free(hier, L)
     P = coarse_basis(hier, L)[f]
@@ -162,6 +151,35 @@ def correction_on_level(hier: Hierarchy, L: int, lam_k: float, u: np.ndarray, tr
     return lam, un
 
 
+def glued(hier: Hierarchy, L: int, lam_k: float, u: np.ndarray, mapper=map):
+    """Steps 1 and 2 of Algorithm 4.1 on level L: the local solutions and the glued function
+    u~ (with the G_{m+1} problem) for the pair (lambda_{h_k}, u_{h_k}) already in V_{h_L}.
+    Returns (u~, [e^j])."""
+    K, M = hier.K[L], hier.M[L]
+    part: LevelPartition = hier.parts[L]
+    Mu = M @ u
+    Ku = K @ u
+    # Step 1 (Eq. Aux_Problem): a(e^j, v) = lambda_k b(u_k, v) - a(u_k, v) for v in V_{0h_{k+1}}(Omega_j)
+    rhs = lam_k * Mu - Ku
+    u_tilde_j, e_list = [], []
+    sols = mapper(local_solve, [(K[loc][:, loc].tocsc(), rhs[loc]) for loc in part.local])
+    for loc, x in zip(part.local, sols):
+        e = np.zeros_like(u)
+        e[loc] = x
+        e_list.append(e)
+        u_tilde_j.append(u + e)                    # u~^j = u_{h_k} + e^j on Omega_j
+    # Step 2: u~ = u~^j on closed G_j, and on G_{m+1} solve Eq. G_m+1_Problem with Dirichlet data u~^j.
+    ut = np.zeros_like(u)
+    for j, g in enumerate(part.g_nodes):
+        ut[g] = u_tilde_j[j][g]
+    S = part.strip
+    if S.size:
+        # a(u~^{m+1}, v) = lambda_k b(u_k, v), v in V_{0h}(G_{m+1}); known values of u~ move to the right.
+        rhs_s = lam_k * Mu[S] - (K[S] @ ut)        # ut is zero on S here
+        ut[S] = spla.splu(K[S][:, S].tocsc()).solve(rhs_s)
+    return ut, e_list
+
+
 @dataclass
 class Result:
     lam: float                 # lambda_{h_n}
@@ -177,15 +195,16 @@ def to_grid(hier: Hierarchy, ell: int, u: np.ndarray) -> np.ndarray:
     return g.reshape(lv.ny + 1, lv.nx + 1)
 
 
-def solve(problem: W.Problem, b: int = 0, trace: bool = False, hier: Hierarchy | None = None) -> Result:
-    """Algorithm 4.2 for batch member b."""
+def solve(problem: W.Problem, b: int = 0, trace: bool = False, hier: Hierarchy | None = None,
+          mapper=map) -> Result:
+    """Algorithm 4.2 for batch member b (`mapper` runs the local solves, see `correction`)."""
     hier = hier or build(problem, b)
     n = problem.levels
     lam, u = global_eigpair(hier, 1)               # step 1: eigenproblem in V_{0h_1}
     lams = [lam]
     traces = []
     for k in range(1, n):                          # step 3: k = 1 .. n-1
-        out = correction(hier, k, lam, u, trace=trace)
+        out = correction(hier, k, lam, u, trace=trace, mapper=mapper)
         lam, u = out[0], out[1]
         if trace:
             traces.append(out[2])

@@ -86,6 +86,34 @@ def test_interior_stencils():
         assert m[d] == pytest.approx(h * h / 12, rel=1e-14)
 
 
+def test_stiffness_row_with_a_different_kappa_on_each_of_six_triangles():
+    """Hand-computed row, independent of the oracle's layout rule: node c = (3, 5) of the finest
+    lattice touches six triangles, L(c) and U(c) of the cell NE of it, U of the cell SE, L of the
+    cell NW, L and U of the cell SW (kappa[cj][ci][t], t = 0 the triangle with the cell's SE
+    corner). On a right triangle with legs h the P1 stiffness couples the two legs' end nodes
+    by -kappa/2 and the hypotenuse's by 0, so each axis edge of c gets the mean of the two
+    triangles it is a leg of, and the diagonal edges nothing."""
+    p = W.kappa_fine_elem(W.unit_square(2, 1, 2, overlap=0), seed=0)
+    kap = np.ones_like(p.kappa)
+    vals = {"Lc": 2.0, "Uc": 3.0, "Us": 5.0, "Lw": 7.0, "Lsw": 11.0, "Usw": 13.0}
+    kap[0, 5, 3, 0], kap[0, 5, 3, 1] = vals["Lc"], vals["Uc"]
+    kap[0, 4, 3, 1] = vals["Us"]
+    kap[0, 5, 2, 0] = vals["Lw"]
+    kap[0, 4, 2, 0], kap[0, 4, 2, 1] = vals["Lsw"], vals["Usw"]
+    kap[0, 4, 3, 0] = kap[0, 5, 2, 1] = 17.0  # the two other triangles of those cells: not at c
+    p.kappa = kap
+    levels = mesh.build_levels(p.cell_in, p.levels, p.H)
+    lv = levels[p.levels]
+    K, _ = fem.assemble(lv, fem.kappa_all_levels(p, levels, 0)[p.levels], p.H)
+    row = _row(K, lv, 3, 5)
+    we, wn = (vals["Lc"] + vals["Us"]) / 2, (vals["Uc"] + vals["Lw"]) / 2
+    ww, ws = (vals["Lw"] + vals["Usw"]) / 2, (vals["Us"] + vals["Lsw"]) / 2
+    assert set(row) == {(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)}
+    assert row[(0, 0)] == pytest.approx(we + wn + ww + ws, rel=1e-14)
+    assert row[(1, 0)] == pytest.approx(-we, rel=1e-14) and row[(0, 1)] == pytest.approx(-wn, rel=1e-14)
+    assert row[(-1, 0)] == pytest.approx(-ww, rel=1e-14) and row[(0, -1)] == pytest.approx(-ws, rel=1e-14)
+
+
 def test_element_matrices_against_quadrature():
     """Brute force: gradients by finite differences of barycentrics, mass by a degree-2 exact rule."""
     rng = np.random.default_rng(1)
