@@ -5,11 +5,20 @@ A step is one whole multilevel eigensolve (Algorithm 4.2: the level-1 eigenprobl
 then every correction step of Algorithm 4.1 with its local problems, gluing, G_{m+1}
 problem and Rayleigh-Ritz) of the unit-square workload with a 16x16 coarse grid, 4x4
 overlapping subdomains and 6 levels (finest 1024x1024, 1,046,529 unknowns), computed
-in the mixed form (FP32 multigrid local solves + FP64 residual refinement).
+in the mixed form (FP32 multigrid local solves, FP64 residuals / inner products /
+Rayleigh-Ritz).
 
 Metric: fine-mesh DOF/s = unknowns of T_{h_n} / seconds per solve, whole job (all ranks).
 Also reported: the same solve in plain FP64 on the GPU, the end-to-end rate through the
-host-buffer C call, the roofline of the dominant kernel and the CPU oracle's rate.
+host-buffer C call, the roofline of the dominant kernel, and two more workloads whose
+working sets exceed the L2 cache ("legs": the 64-subdomain L-shape at 8 levels, 12.6M
+unknowns, and a batch of 256 problems with a coefficient per coarse cell, 16.6M
+unknowns), each with its own DOF/s, accuracy against the stored oracle eigenvalues and the
+HBM roofline of its local-solve (multigrid) kernels; then the CPU oracle's rate.
+
+Schedules (cycle and sweep counts, V-cycle form) are the autotuner's choices stored in
+paper_1401_4969_gb300/schedules.json for this device; a workload or device without a
+stored schedule is tuned at start (untimed).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mlev|reference]
 """
@@ -29,33 +38,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fine-mesh DOF/s per multilevel eigensolve at rel lambda err <=1e-8, vs plain FP64 GPU; HBM %"
-WORKLOAD = "c2: unit square, coarse 16x16, 4x4 subdomains (overlap 1, delta=H/2), 6 levels, finest 1024x1024"
 REL_TOL = 1e-8
-
-
-# Schedules (cycle and sweep counts) come from the autotuner: the fastest schedule whose
-# eigenvalue stays within 0.25 x the 1e-8 bar of a conservative FP64 GPU solve, tuned
-# separately for the mixed path and for the plain FP64 comparator (equal accuracy target).
-# The timed result is then checked against the stored oracle eigenvalue.
-TUNED = {"mixed": None, "fp64": None}
-
-
-def autotune_safety():
-    from paper_1401_4969_gb300 import autotune
-
-    return autotune.SAFETY
-
-
-def mixed_opts(mlev, graph=1):
-    from paper_1401_4969_gb300 import autotune
-
-    return autotune.apply(mlev.default_opts(precision=mlev.PREC_MIXED, use_graph=graph), TUNED["mixed"].opts)
-
-
-def fp64_opts(mlev, graph=1):
-    from paper_1401_4969_gb300 import autotune
-
-    return autotune.apply(mlev.default_opts(precision=mlev.PREC_FP64, use_graph=graph), TUNED["fp64"].opts)
+WORKLOADS = {
+    "c2": "c2: unit square, coarse 16x16, 4x4 subdomains (overlap 1, delta=H/2), 6 levels, finest 1024x1024",
+    "c3": "c3: L-shape (-1,1)^2 minus [0,1)x(-1,0], H=1/8, 64 guillotine subdomains (overlap 1-2, delta=H/4), "
+          "8 levels, finest h=1/2048",
+    "c4": "c4: 256 problems, unit square, kappa per 16x16 coarse cell log-uniform in [1,10], 4x4 subdomains, "
+          "4 levels, finest 256x256 each",
+}
+GOLDEN = {"c2": "oracle_c2.json", "c3": "oracle_c3.json", "c4": "oracle_c4.json"}
+# kernel families of the local solves (step 1's auxiliary problems and the G_{m+1} problem)
+LOCAL_FAMILIES = ("mg_gather", "mg_smooth", "mg_restrict", "mg_prolong", "mg_coarsest", "mixed_accumulate",
+                  "mixed_refine_residual", "mg_down_fused", "mg_up_fused", "mg_tail")
 
 
 # ------------------------------------------------------------------ helpers
@@ -119,54 +113,83 @@ def stop_clock_sampler(proc, fh, path, gpu_index):
             "reasons": sorted(reasons), "samples": len(load)}
 
 
+KERNEL_SOURCES = ("kern_mg.cu", "kern_mgfused.cu", "kern_mgreg.cu", "kern_common.cuh", "kern_blk.cuh", "kern_tail.cuh")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("kern_mg.cu", "kern_mgfused.cu", "kern_common.cuh", "kern_blk.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1401_4969_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it still matches the source."""
+def ncu_traffic(workload, family):
+    """Per-launch DRAM bytes of a kernel family's largest launch on a workload, from the
+    committed ncu summary, if the multigrid sources are unchanged since it was taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    e = d.get(kernel)
+    e = d.get(f"{workload}/{family}")
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch_full_size")
+    return {k: e[k] for k in ("dram_bytes_per_launch", "algorithmic_bytes_per_launch", "launch", "command_note")
+            if k in e}
 
 
-def golden_lambda():
-    path = os.path.join(ROOT, "tests", "golden", "oracle_c2.json")
+def golden_lambdas(name):
+    """Stored oracle eigenvalues {batch member: lambda_{h_n}} of a workload (None if not stored)."""
+    path = os.path.join(ROOT, "tests", "golden", GOLDEN[name])
+    if not os.path.exists(path):
+        return None
     with open(path) as f:
-        return json.load(f)["members"]["0"]["lam"]
+        d = json.load(f)
+    return {int(b): m["lam"] for b, m in d["members"].items()}
 
 
 # ------------------------------------------------------------------ CPU oracle legs
 ORACLE_SAMPLE_LEVELS = {"cpu_baseline": 5, "reference": 4}
 
+_ORACLE_SCRIPT = r"""
+import sys, time, json, os, multiprocessing as mp
+sys.path.insert(0, %(root)r)
+import workloads as W
+from oracle import multilevel as ML
 
-def oracle_sample_cmd(levels):
-    code = (
-        "import sys, time, json; sys.path.insert(0, %r)\n"
-        "import workloads as W\n"
-        "from oracle import multilevel as ML\n"
-        "p = W.config2(levels=%d)\n"
-        "t = time.perf_counter(); h = ML.build(p); r = ML.solve(p, hier=h); dt = time.perf_counter() - t\n"
-        "n = int((~h.levels[p.levels].boundary).sum())\n"
-        "print(json.dumps({'seconds': dt, 'dofs': n, 'lam': r.lam}))\n" % (ROOT, levels))
+def run(levels, pool):
+    p = W.config2(levels=levels)
+    t = time.perf_counter()
+    h = ML.build(p)
+    r = ML.solve(p, hier=h, mapper=pool.map if pool else map)
+    dt = time.perf_counter() - t
+    return dt, int((~h.levels[p.levels].boundary).sum()), r.lam
+
+if __name__ == "__main__":
+    levels, npool = %(levels)d, %(npool)d
+    out = {}
+    dt, n, lam = run(levels, None)
+    out["single"] = {"seconds": dt, "dofs": n, "lam": lam}
+    if npool > 1:
+        with mp.get_context("spawn").Pool(npool) as pool:
+            dt, n, lam = run(levels, pool)
+        out["pool"] = {"seconds": dt, "dofs": n, "lam": lam, "processes": npool}
+    print(json.dumps(out))
+"""
+
+
+def run_oracle_sample(levels, npool=1):
+    """The oracle (Algorithm 4.2, sparse direct local solves, dense Rayleigh-Ritz) on the C2
+    geometry truncated to `levels`, in a process of its own with BLAS threads 1: once in one
+    process, and once with the local solves of each level mapped over a pool of `npool`
+    processes (the paper's one-processor-per-subdomain model)."""
+    path = os.path.join(tempfile.gettempdir(), "mlev_oracle_sample.py")
+    with open(path, "w") as f:
+        f.write(_ORACLE_SCRIPT % {"root": ROOT, "levels": levels, "npool": npool})
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    return [sys.executable, "-c", code], env
-
-
-def run_oracle_sample(levels):
-    cmd, env = oracle_sample_cmd(levels)
-    out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
+    out = subprocess.run([sys.executable, path], env=env, capture_output=True, text=True, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
@@ -179,7 +202,7 @@ def reference_arm(args):
         run_oracle_sample(lv)
     times, dofs = [], None
     for _ in range(args.steps):
-        r = run_oracle_sample(lv)
+        r = run_oracle_sample(lv)["single"]
         times.append(r["seconds"])
         dofs = r["dofs"]
     ms = 1e3 * statistics.mean(times)
@@ -189,11 +212,35 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + f" (sample: {lv} levels)", "global_batch": 1, "flush": "none (CPU)"},
+            "config": {"workload": WORKLOADS["c2"] + f" (sample: {lv} levels)", "global_batch": 1,
+                       "flush": "none (CPU)"},
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def cpu_baseline_leg():
+    """The oracle as it stands on a bounded sample of the workload (5 levels of the same
+    geometry), one process and a pool of os.cpu_count() processes, run after the GPU legs."""
+    lv = ORACLE_SAMPLE_LEVELS["cpu_baseline"]
+    ncores = os.cpu_count() or 1
+    try:
+        r = run_oracle_sample(lv, ncores)
+    except Exception as e:  # report, do not hide
+        return {"error": str(e)[-300:]}
+    s = r["single"]
+    out = {"value": s["dofs"] / s["seconds"], "unit": "DOF/s", "cores": 1, "kind": "oracle",
+           "sample": f"oracle Algorithm 4.2 on the same geometry truncated to {lv} levels ({s['dofs']} unknowns), "
+                     f"{s['seconds']:.1f} s, one process, BLAS threads = 1",
+           "host_cores": ncores}
+    if "pool" in r:
+        q = r["pool"]
+        out["pool"] = {"value": q["dofs"] / q["seconds"], "unit": "DOF/s", "cores": q["processes"],
+                       "seconds": q["seconds"], "lambda_identical": q["lam"] == s["lam"],
+                       "sample": "same sample, the local solves of each level over a process pool "
+                                 f"of {q['processes']} (one per host core)"}
+    return out
 
 
 def time_adjoint(mlev, W, torch, reps=5):
@@ -225,7 +272,152 @@ def time_adjoint(mlev, W, torch, reps=5):
             "dofs": 511 * 511}
 
 
-# ------------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------------ GPU legs
+def schedule(name, problem, precision, device, solver):
+    """(opts dict, source): the stored autotuner choice for this workload and device, else tuned now."""
+    import torch
+
+    from paper_1401_4969_gb300 import autotune
+
+    dev_name = torch.cuda.get_device_name(device)
+    e = autotune.committed(name, problem, precision, REL_TOL, dev_name)
+    if e:
+        return dict(e["opts"]), "schedules.json (autotuner, stored)"
+    r = autotune.tune(problem, precision=precision, target_rel=REL_TOL, device=device, solver=solver)
+    return dict(r.opts), "autotuner (tuned at start, untimed)"
+
+
+def make_opts(mlev, precision, sched, graph=1):
+    from paper_1401_4969_gb300 import autotune
+
+    return autotune.apply(mlev.default_opts(precision=precision, use_graph=graph), sched)
+
+
+class Timer:
+    """CUDA-event timing of whole solves on one stream, L2 flushed (512 MB write) before each."""
+
+    def __init__(self, torch, stream, dist):
+        self.torch, self.stream, self.dist = torch, stream, dist
+        self.flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def __call__(self, solver, opts, lam, steps, warmup):
+        from paper_1401_4969_gb300 import replicas
+
+        torch = self.torch
+        for w in range(warmup):
+            self.flush.fill_(w & 0xFF)
+            solver.solve_into(opts, lam, None, self.stream)
+        self.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        for k in range(steps):
+            self.flush.fill_(k & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            solver.solve_into(opts, lam, None, self.stream)
+            e1.record(self.stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        self.barrier()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        return replicas.max_over_ranks(ms, self.dist, "cuda")
+
+
+def profile_families(mlev, solver, opts, timer):
+    """Per-kernel-family CUDA-event times and algorithmic bytes of one solve (second of two)."""
+    op = mlev.default_opts()
+    for f, _ in op._fields_:
+        setattr(op, f, getattr(opts, f))
+    op.use_graph = 0
+    op.profile = 1
+    lam, _ = solver.alloc_outputs()
+    prof = None
+    for _ in range(2):
+        timer.flush.fill_(1)
+        solver.solve_into(op, lam, None, timer.stream)
+        prof = mlev.profile_read(solver)
+    timer.torch.cuda.synchronize()
+    return [r for r in prof if r["launches"]]
+
+
+def roofline_of(name, rows, peak, peak_kind, total_ms):
+    """HBM roofline of a set of kernel-family rows: algorithmic bytes / event time."""
+    by = sum(r["bytes"] for r in rows)
+    ms = sum(r["ms"] for r in rows)
+    launches = sum(r["launches"] for r in rows)
+    ach = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "launches_per_step": launches, "algorithmic_bytes_per_launch": by / max(launches, 1),
+            "avg_launch_us": 1e3 * ms / max(launches, 1), "share_of_step": ms / total_ms if total_ms else None}
+
+
+def accuracy(name, lam_np):
+    gold = golden_lambdas(name)
+    if not gold:
+        return {"rel_err": None, "note": "no stored oracle eigenvalue for this workload"}
+    errs = {b: abs(float(lam_np[b]) - g) / g for b, g in gold.items() if b < len(lam_np)}
+    worst = max(errs, key=errs.get)
+    return {"rel_err": errs[worst], "members_checked": len(errs), "worst_member": worst,
+            "lambda": float(lam_np[worst]), "lambda_oracle": gold[worst], "tol": REL_TOL}
+
+
+def gpu_leg(name, timer, args, device, peak, peak_kind, steps, warmup, with_fp64=True):
+    """One workload: stored schedules, timed mixed and FP64 solves, accuracy, profile, roofline."""
+    import workloads as W
+    from paper_1401_4969_gb300 import mlev
+
+    rank, _, world = dist_env()
+    p = W.CONFIGS[name]()
+    solver = mlev.Solver(p, device=device)
+    info = solver.info()
+    n_units = info["n_fine"] * p.batch
+    sm, src = schedule(name, p, mlev.PREC_MIXED, device, solver)
+    om = make_opts(mlev, mlev.PREC_MIXED, sm)
+    lam, _ = solver.alloc_outputs(want_u=False)
+    rep = solver.solve_into(make_opts(mlev, mlev.PREC_MIXED, sm, graph=0), lam, None, timer.stream, report=True)
+    ms = timer(solver, om, lam, steps, warmup)
+    lam_mixed = lam.cpu().numpy().copy()
+    leg = {"workload": WORKLOADS[name], "dofs_per_problem": info["n_fine"], "batch": p.batch,
+           "local_unknowns_per_problem": info["n_local_fine"], "strip_unknowns_per_problem": info["n_strip_fine"],
+           "value": world * n_units / (ms / 1e3), "unit": "DOF/s", "ms_per_step": ms, "steps": steps,
+           "precision": "mixed", "opts": sm, "schedule_source": src, "kernel_launches": rep["kernel_launches"],
+           "accuracy": accuracy(name, lam_mixed)}
+    if with_fp64:
+        s64, src64 = schedule(name, p, mlev.PREC_FP64, device, solver)
+        ms64 = timer(solver, make_opts(mlev, mlev.PREC_FP64, s64), lam, max(3, steps // 4), 2)
+        lam64 = lam.cpu().numpy().copy()
+        leg["fp64_gpu"] = {"value": world * n_units / (ms64 / 1e3), "unit": "DOF/s", "ms_per_step": ms64,
+                           "opts": s64, "schedule_source": src64, "speedup_mixed_over_fp64": ms64 / ms,
+                           "accuracy": accuracy(name, lam64)}
+    prof = profile_families(mlev, solver, om, timer)
+    total = sum(r["ms"] for r in prof)
+    local = [r for r in prof if r["name"] in LOCAL_FAMILIES]
+    dom_local = max(local, key=lambda r: r["ms"]) if local else None
+    leg["profile"] = [{k: r[k] for k in ("name", "launches", "ms", "bytes")} for r in prof]
+    leg["profile_total_ms"] = total
+    leg["local_solve_roofline"] = roofline_of("local-solve kernel families " + "+".join(r["name"] for r in local),
+                                              local, peak, peak_kind, total)
+    if dom_local:
+        rl = roofline_of(dom_local["name"], [dom_local], peak, peak_kind, total)
+        rl["traffic"] = ncu_traffic(name, dom_local["name"])
+        leg["dominant_local_roofline"] = rl
+    leg["_solver"] = solver
+    leg["_lam"] = lam
+    leg["_lam_np"] = lam_mixed
+    leg["_n_units"] = n_units
+    return leg
+
+
+def public(leg):
+    return {k: v for k, v in leg.items() if not k.startswith("_")}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -235,7 +427,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel profiled pass")
+    ap.add_argument("--no-legs", action="store_true", help="skip the L-shape and 256-problem workloads")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing (512x512 kappa workload)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -251,178 +443,107 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    cpu_base = None
-    if rank == 0 and not args.no_cpu_baseline:
-        # spawned before any CUDA work of this process matters; its own process, no CUDA
-        cpu_base = subprocess.Popen(oracle_sample_cmd(ORACLE_SAMPLE_LEVELS["cpu_baseline"])[0],
-                                    env=oracle_sample_cmd(ORACLE_SAMPLE_LEVELS["cpu_baseline"])[1],
-                                    stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+    from paper_1401_4969_gb300 import mlev, replicas
 
-    import workloads as W
-    from paper_1401_4969_gb300 import autotune, mlev, replicas
-
-    p = W.config2()
-    solver = mlev.Solver(p, device=local_rank)
-    info = solver.info()
-    # untimed: pick the schedules (cached per problem / precision / target / device)
-    TUNED["mixed"] = autotune.tune(p, precision=mlev.PREC_MIXED, target_rel=REL_TOL, device=local_rank,
-                                   solver=solver)
-    if not args.no_fp64:
-        TUNED["fp64"] = autotune.tune(p, precision=mlev.PREC_FP64, target_rel=REL_TOL, device=local_rank,
-                                      solver=solver)
-    n_units = info["n_fine"] * p.batch
+    peak, peak_kind = measured_peaks()
     stream = torch.cuda.current_stream()
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
-    lam, _ = solver.alloc_outputs(want_u=False)
+    timer = Timer(torch, stream, dist)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def timed(opts, steps, warmup):
-        for w in range(warmup):
-            flush.fill_(w & 0xFF)
-            solver.solve_into(opts, lam, None, stream)
-        barrier()
-        torch.cuda.synchronize()
-        evs = []
-        for k in range(steps):
-            flush.fill_(k & 0xFF)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            solver.solve_into(opts, lam, None, stream)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        barrier()
-        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
-        return replicas.max_over_ranks(ms, dist, "cuda")
-
-    om = mixed_opts(mlev)
-    rep = solver.solve_into(mixed_opts(mlev, graph=0), lam, None, stream, report=True)
-    launches_per_step = rep["kernel_launches"]
-    # nvidia-smi samples of the timed region (MLEV_BENCH_OUT: keep them in that directory)
+    # headline: the 6-level unit-square workload (timed with nvidia-smi clock samples)
     clk_path = os.path.join(os.environ.get("MLEV_BENCH_OUT", tempfile.gettempdir()), f"bench_clocks_r{rank}.csv")
     sampler, fh = start_clock_sampler(clk_path)
-    ms_mixed = timed(om, args.steps, args.warmup)
+    head = gpu_leg("c2", timer, args, local_rank, peak, peak_kind, args.steps, args.warmup,
+                   with_fp64=not args.no_fp64)
     clocks = stop_clock_sampler(sampler, fh, clk_path, local_rank)
-    value = world * n_units / (ms_mixed / 1e3)
-    lam_mixed = float(lam[0].item())
+    solver = head["_solver"]
+    p = solver.problem
+    launches_per_step = head["kernel_launches"]
 
-    ms_fp64 = None
-    lam_fp64 = None
-    if not args.no_fp64:
-        of = fp64_opts(mlev)
-        ms_fp64 = timed(of, max(3, args.steps // 4), 2)
-        lam_fp64 = float(lam[0].item())
-
-    if args.no_e2e or args.no_profile:
-        if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
-                              "warmup": args.warmup, "ms_per_step": ms_mixed, "partial": "e2e/profile legs skipped",
-                              "gpu_launches": launches_per_step * args.steps}), flush=True)
-        if dist is not None:
-            dist.destroy_process_group()
-        return 0
-
-    # end to end through the host-buffer entry point: plan tables in, lambda and u_{h_n} out
-    ny, nx = solver.grid_shape()
-    lam_h = torch.empty(p.batch, dtype=torch.float64, pin_memory=True).numpy()
-    u_h = torch.empty((p.batch, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
-    oh = mixed_opts(mlev, graph=1)  # graph replay, as in the device-timed leg
-    io = solver.solve_host(oh, lam_h, u_h, report=True)
-    solver.solve_host(oh, lam_h, u_h)
-    e2e_t = []
-    for k in range(max(3, args.steps // 2)):
-        flush.fill_(k & 0xFF)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the host-buffer entry point: plan tables in, lambda and u_{h_n} out
+        ny, nx = solver.grid_shape()
+        lam_h = torch.empty(p.batch, dtype=torch.float64, pin_memory=True).numpy()
+        u_h = torch.empty((p.batch, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+        oh = make_opts(mlev, mlev.PREC_MIXED, head["opts"], graph=1)  # graph replay, as in the device-timed leg
+        io = solver.solve_host(oh, lam_h, u_h, report=True)
         solver.solve_host(oh, lam_h, u_h)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_ms = replicas.max_over_ranks(1e3 * statistics.mean(e2e_t), dist, "cuda")
-    e2e_lambda = float(lam_h[0])
-    h2d, d2h = int(io["h2d_bytes"]), int(io["d2h_bytes"])
+        e2e_t = []
+        for k in range(max(3, args.steps // 2)):
+            timer.flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            solver.solve_host(oh, lam_h, u_h)
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_ms = replicas.max_over_ranks(1e3 * statistics.mean(e2e_t), dist, "cuda")
+        e2e = {"value": world * head["_n_units"] / (e2e_ms / 1e3), "unit": "DOF/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": int(io["h2d_bytes"]), "d2h_bytes_per_step": int(io["d2h_bytes"]),
+               "call": "mlev_solve_host (plan tables H2D, graph-replayed solve, lambda + u_{h_n} D2H, "
+                       "pinned host buffers)",
+               "lambda_matches_device_path": bool(float(lam_h[0]) == float(head["_lam_np"][0]))}
+    solver.close()
 
-    # profiled pass: per-kernel-family CUDA-event times on the solve's stream
-    op = mixed_opts(mlev, graph=0)
-    op.profile = 1
-    prof = None
-    for _ in range(2):
-        flush.fill_(1)
-        solver.solve_into(op, lam, None, stream)
-        prof = mlev.profile_read(solver)
-    torch.cuda.synchronize()
+    legs = {}
+    if not args.no_legs:
+        for name in ("c3", "c4"):
+            leg = gpu_leg(name, timer, args, local_rank, peak, peak_kind, min(args.steps, 10), 3,
+                          with_fp64=not args.no_fp64)
+            leg["_solver"].close()
+            legs[name] = public(leg)
+            del leg
+            torch.cuda.empty_cache()
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    adjoint = None if args.no_adjoint else time_adjoint(mlev, W, torch)
-    peak, peak_kind = measured_peaks()
-    dom = max(prof, key=lambda r: r["ms"])
+    adjoint = None if args.no_adjoint else time_adjoint(mlev, W_module(), torch)
+    prof = head["profile"]
+    total_prof_ms = head["profile_total_ms"]
     with_bytes = [r for r in prof if r["bytes"] > 0]
+    dom = max(prof, key=lambda r: r["ms"])
     dom_hbm = max(with_bytes, key=lambda r: r["ms"])
-    ach = (dom_hbm["bytes"] / dom_hbm["launches"]) / (dom_hbm["ms"] / dom_hbm["launches"] / 1e3) / 1e9
-    traffic = ncu_traffic(dom_hbm["name"])
-    total_prof_ms = sum(r["ms"] for r in prof)
-    roofline = {"bound": "hbm", "kernel": dom_hbm["name"], "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": traffic, "launches_per_step": dom_hbm["launches"],
-                "algorithmic_bytes_per_launch": dom_hbm["bytes"] / dom_hbm["launches"],
-                "avg_launch_us": 1e3 * dom_hbm["ms"] / dom_hbm["launches"],
-                "share_of_step": dom_hbm["ms"] / total_prof_ms,
-                "top_kernel_by_time": dom["name"],
-                "note": "working set of this workload (~90 MB) is L2-resident (129 MB L2); achieved is "
-                        "algorithmic bytes over event time, so it can exceed the HBM peak"}
-
-    gold = golden_lambda()
+    roofline = roofline_of(dom_hbm["name"], [dom_hbm], peak, peak_kind, total_prof_ms)
+    roofline["traffic"] = (ncu_traffic("c2", dom_hbm["name"]) or {}).get("dram_bytes_per_launch")
+    roofline["top_kernel_by_time"] = dom["name"]
+    roofline["note"] = ("the 1M-unknown workload's working set (~100 MB) stays in the 129 MB L2 and most of its "
+                        "launches are small grids: achieved is algorithmic bytes over event time; the HBM-bound "
+                        "measurements are the legs' local_solve_roofline")
     line = {
-        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": head["value"], "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": p.batch * world, "dofs_per_problem": info["n_fine"],
+        "config": {"workload": WORKLOADS["c2"], "global_batch": p.batch * world, "dofs_per_problem": head["dofs_per_problem"],
                    "parallelism": f"replicas{world}" if world > 1 else "single", "precision": "mixed",
                    "flush": "L2 flushed (512 MB write) before every timed step",
-                   "opts": dict(TUNED["mixed"].opts),
-                   "opts_fp64": None if TUNED["fp64"] is None else dict(TUNED["fp64"].opts),
-                   "autotune": {"target_rel": REL_TOL, "safety": autotune_safety(),
-                                "reference": "FP64 GPU solve, 6 V-cycles x 2 passes",
-                                "mixed_trials": len(TUNED["mixed"].trials),
-                                "mixed_err_vs_reference": TUNED["mixed"].err,
-                                "fp64_err_vs_reference": None if TUNED["fp64"] is None else TUNED["fp64"].err}},
-        "accuracy": {"lambda": lam_mixed, "lambda_oracle": gold, "rel_err": abs(lam_mixed - gold) / gold,
-                     "tol": REL_TOL,
-                     "fp64_rel_err": None if lam_fp64 is None else abs(lam_fp64 - gold) / gold},
-        "fp64_gpu": None if ms_fp64 is None else {"value": world * n_units / (ms_fp64 / 1e3), "unit": "DOF/s",
-                                                  "ms_per_step": ms_fp64,
-                                                  "speedup_mixed_over_fp64": ms_fp64 / ms_mixed},
-        "e2e": {"value": world * n_units / (e2e_ms / 1e3), "unit": "DOF/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "call": "mlev_solve_host (plan tables H2D, graph-replayed solve, lambda + u_{h_n} D2H, pinned host buffers)",
-                "lambda_matches_device_path": e2e_lambda == lam_mixed},
+                   "opts": head["opts"], "schedule_source": head["schedule_source"],
+                   "refinement": ("one FP32 pass per local / G_{m+1} problem with this schedule (refine_passes = 1): "
+                                  "no FP64 residual-correction pass runs in the timed solve; FP64 holds the global "
+                                  "fields, residual right-hand sides, glue, inner products and Rayleigh-Ritz")},
+        "accuracy": head["accuracy"],
+        "fp64_gpu": head.get("fp64_gpu"),
+        "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
-        "profile": [{k: r[k] for k in ("name", "launches", "ms", "bytes")} for r in prof if r["launches"]],
+        "local_solve_roofline": head["local_solve_roofline"],
+        "profile": prof,
         "clocks": clocks,
+        "legs": legs,
         "adjoint": adjoint,
     }
-    if cpu_base is not None:
-        out, err = cpu_base.communicate()
-        try:
-            r = json.loads(out.strip().splitlines()[-1])
-            line["cpu_baseline"] = {
-                "value": r["dofs"] / r["seconds"], "unit": "DOF/s", "cores": 1, "kind": "oracle",
-                "sample": f"oracle Algorithm 4.2 on the same geometry truncated to "
-                          f"{ORACLE_SAMPLE_LEVELS['cpu_baseline']} levels ({r['dofs']} unknowns), "
-                          f"{r['seconds']:.1f} s, one process, BLAS threads = 1"}
-        except Exception as e:  # report, do not hide
-            line["cpu_baseline"] = {"error": f"{e}: {err[-300:]}"}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_leg()  # after every GPU leg: no contention for the host
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def W_module():
+    import workloads
+
+    return workloads
 
 
 if __name__ == "__main__":

@@ -216,3 +216,61 @@ def apply(opts_struct, tuned: dict):
     for k, v in tuned.items():
         setattr(opts_struct, k, float(v) if k in FLOAT_KEYS else int(v))
     return opts_struct
+
+
+# ------------------------------------------------------------------ committed schedules
+COMMITTED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "schedules.json")
+
+
+def committed_key(workload: str, precision: int, target_rel: float, device_name: str) -> str:
+    return f"{workload}/p{precision}/t{target_rel:g}/{device_name}"
+
+
+def committed(workload: str, problem, precision: int, target_rel: float, device_name: str,
+              path: str | None = None) -> dict | None:
+    """The schedule this tuner chose for a named workload on a device and stored in
+    schedules.json (None if absent, or if the workload's inputs changed since)."""
+    entry = _load_cache(path or COMMITTED).get(committed_key(workload, precision, target_rel, device_name))
+    if not entry or entry.get("signature") != problem_signature(problem):
+        return None
+    return entry
+
+
+def tune_committed(workloads, out: str, target_rel: float = 1e-8, device: int = 0):
+    """Tune each named workload of workloads.CONFIGS in both precisions and store the results
+    (opts, time, error, problem signature) in `out`, keyed as committed() reads them."""
+    import torch
+
+    import workloads as W
+
+    from . import mlev
+
+    dev_name = torch.cuda.get_device_name(device)
+    data = _load_cache(out)
+    for name in workloads:
+        p = W.CONFIGS[name]()
+        s = mlev.Solver(p, device=device)
+        try:
+            for prec in (mlev.PREC_MIXED, mlev.PREC_FP64):
+                r = tune(p, precision=prec, target_rel=target_rel, device=device, use_cache=False, solver=s)
+                data[committed_key(name, prec, target_rel, dev_name)] = {
+                    "opts": r.opts, "ms": r.ms, "err": r.err, "signature": problem_signature(p), "problem": p.name,
+                    "trials": len(r.trials)}
+                print(name, prec, r.opts, "%.3f ms" % r.ms, "err %.2e" % r.err, flush=True)
+        finally:
+            s.close()
+        _store_cache(out, data)
+    return data
+
+
+if __name__ == "__main__":
+    import argparse
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    ap = argparse.ArgumentParser(description="tune named workloads and store their schedules")
+    ap.add_argument("workloads", nargs="+")
+    ap.add_argument("--out", default=COMMITTED)
+    ap.add_argument("--target", type=float, default=1e-8)
+    a = ap.parse_args()
+    tune_committed(a.workloads, a.out, a.target)

@@ -252,7 +252,7 @@ struct Launcher {
   // the register-blocked FP32 down / up kernels replace the shared-memory ones where they apply
   template <typename T>
   bool use_reg(const std::vector<TileList>* rl) const {
-    return sizeof(T) == 4 && rl && rkernels_support(P.kappa_kind, o.pre_smooth, o.post_smooth);
+    return sizeof(T) == 4 && rl && rkernels_support(P.kappa_kind, o.pre_smooth, o.post_smooth, o.omega);
   }
 
   template <typename T>
@@ -540,7 +540,8 @@ struct Launcher {
       // only where the inner-product kernel, every block then holding the factor's shared
       // memory, still runs in one wave (a batch of many problems would lose occupancy there)
       const size_t pre_smem = rr_prefactor_smem(P.nhb, P.bw);
-      const long long aug_blocks = (long long)B * (P.ncx * P.ncy + 1);
+      const long long aug_cells = (long long)B * P.ncx * P.ncy;
+      const long long aug_blocks = L <= 5 ? B + (aug_cells + 7) / 8 : aug_cells + B;  // warp or block per cell
       // (per block: the factor's dynamic memory, the kernel's 22.6 KB of static staging and the
       // 1 KB the runtime reserves)
       const long long aug_slots = (long long)ctx->sm_count * (long long)(ctx->smem_per_sm / (pre_smem + 24 * 1024));

@@ -123,9 +123,70 @@ __global__ void __launch_bounds__(256) k_strip_update(DevGeom G, GlobalLayout gl
 }
 
 // Step 3 inputs on one T_H cell: alpha = a(u~,u~), beta = b(u~,u~), sigma = sum of u~,
-// and the cell's share of g_a = P_H^T K u~, g_b = P_H^T M u~ at its four corners.
+// and the cell's share of g_a = P_H^T K u~, g_b = P_H^T M u~ at its four corners, summed
+// by the nt threads tid = 0 .. nt-1 into acc (each thread's partial sums).
 // partials[p][cell][12]: 0 alpha, 1 beta, 2 sigma, 3..6 K-part at corners 00,10,01,11,
 // 7..10 M-part at corners 00,10,01,11.
+template <int KK>
+__device__ __forceinline__ void aug_cell(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, int p, int ci,
+                                         int cj, int tid, int nt, double (&acc)[11]) {
+#pragma unroll
+  for (int k = 0; k < 11; ++k) acc[k] = 0.0;
+  if (!G.cell_in[cj * G.ncx + ci]) return;
+  const int L = a.L;
+  const int nx = gl.nx[lidx(L)], ny = gl.ny[lidx(L)], pitch = gl.pitch[lidx(L)];
+  const int S = 1 << L;
+  const double invS = pow2(-L);
+  const double* u = a.ut + (long long)p * gl.bstride;
+  // Thread layout: a fixed column ri of the cell (s = ri / S) and every nt/S-th row. The
+  // hats of the cell's corners are linear in t = rj / S on each triangle (lower rj <= ri:
+  // 1 - s, s - t, 0, t; upper: 1 - t, 0, t - s, s), so per thread and column it suffices
+  // to sum ku, t ku, mu, t mu over the lower and the upper nodes; the weights are applied
+  // once per column and h^2 / 12 once at the end.
+  const int cstep = S < nt ? S : nt, rstep = S < nt ? nt / S : 1;
+  for (int ri = tid % cstep; ri < S; ri += cstep) {
+    const double s = ri * invS, dt = rstep * invS;
+    double skl = 0.0, tkl = 0.0, sml = 0.0, tml = 0.0, sku = 0.0, tku = 0.0, smu = 0.0, tmu = 0.0;
+    int rj = S < nt ? tid / S : 0;
+    double t = rj * invS;
+    for (; rj < S; rj += rstep, t += dt) {
+      const int i = (ci << L) + ri, j = (cj << L) + rj;
+      if (!is_free(G, L, nx, ny, i, j)) continue;
+      const long long c = (long long)j * pitch + i;
+      const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
+      const double uc = u[c];
+      const double ku = apply_k<double, double>(u, c, pitch, w);
+      const double mu = apply_m12<double, double>(u, c, pitch);  // M u / (h^2 / 12)
+      acc[0] += uc * ku;
+      acc[1] += uc * mu;
+      acc[2] += uc;
+      if (rj > ri) {  // upper triangle
+        sku += ku;
+        tku += t * ku;
+        smu += mu;
+        tmu += t * mu;
+      } else {
+        skl += ku;
+        tkl += t * ku;
+        sml += mu;
+        tml += t * mu;
+      }
+    }
+    acc[3] += (1.0 - s) * skl + sku - tku;
+    acc[4] += s * skl - tkl;
+    acc[5] += tku - s * sku;
+    acc[6] += tkl + s * sku;
+    acc[7] += (1.0 - s) * sml + smu - tmu;
+    acc[8] += s * sml - tml;
+    acc[9] += tmu - s * smu;
+    acc[10] += tml + s * smu;
+  }
+  acc[1] *= a.m12;
+#pragma unroll
+  for (int k = 7; k < 11; ++k) acc[k] *= a.m12;
+}
+
+// One block of 256 threads per T_H cell (cells of 64 x 64 fine nodes or more).
 template <int KK, bool PRE>
 __global__ void __launch_bounds__(256) k_aug(DevGeom G, GlobalLayout gl, LevelArgs a, double* partials,
                                              RRPrefactor pf) {
@@ -146,65 +207,45 @@ __global__ void __launch_bounds__(256) k_aug(DevGeom G, GlobalLayout gl, LevelAr
   }
   const long long q = (long long)blockIdx.x - npre;
   const int ncell = G.ncx * G.ncy;
-  const int p = (int)(q / ncell), ci = (int)(q % ncell) % G.ncx, cj = (int)(q % ncell) / G.ncx, L = a.L;
+  const int p = (int)(q / ncell), ci = (int)(q % ncell) % G.ncx, cj = (int)(q % ncell) / G.ncx;
   double acc[11];
-#pragma unroll
-  for (int k = 0; k < 11; ++k) acc[k] = 0.0;
-  const int nx = gl.nx[lidx(L)], ny = gl.ny[lidx(L)], pitch = gl.pitch[lidx(L)];
-  const int S = 1 << L;
-  const double invS = pow2(-L);
-  const double* u = a.ut + (long long)p * gl.bstride;
-  if (G.cell_in[cj * G.ncx + ci]) {
-    // Thread layout: a fixed column ri of the cell (s = ri / S) and every nt/S-th row. The
-    // hats of the cell's corners are linear in t = rj / S on each triangle (lower rj <= ri:
-    // 1 - s, s - t, 0, t; upper: 1 - t, 0, t - s, s), so per thread and column it suffices
-    // to sum ku, t ku, mu, t mu over the lower and the upper nodes; the weights are applied
-    // once per column and h^2 / 12 once at the end.
-    const int nt = blockDim.x;
-    const int cstep = S < nt ? S : nt, rstep = S < nt ? nt / S : 1;
-    for (int ri = threadIdx.x % cstep; ri < S; ri += cstep) {
-      const double s = ri * invS, dt = rstep * invS;
-      double skl = 0.0, tkl = 0.0, sml = 0.0, tml = 0.0, sku = 0.0, tku = 0.0, smu = 0.0, tmu = 0.0;
-      int rj = S < nt ? threadIdx.x / S : 0;
-      double t = rj * invS;
-      for (; rj < S; rj += rstep, t += dt) {
-        const int i = (ci << L) + ri, j = (cj << L) + rj;
-        if (!is_free(G, L, nx, ny, i, j)) continue;
-        const long long c = (long long)j * pitch + i;
-        const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
-        const double uc = u[c];
-        const double ku = apply_k<double, double>(u, c, pitch, w);
-        const double mu = apply_m12<double, double>(u, c, pitch);  // M u / (h^2 / 12)
-        acc[0] += uc * ku;
-        acc[1] += uc * mu;
-        acc[2] += uc;
-        if (rj > ri) {  // upper triangle
-          sku += ku;
-          tku += t * ku;
-          smu += mu;
-          tmu += t * mu;
-        } else {
-          skl += ku;
-          tkl += t * ku;
-          sml += mu;
-          tml += t * mu;
-        }
-      }
-      acc[3] += (1.0 - s) * skl + sku - tku;
-      acc[4] += s * skl - tkl;
-      acc[5] += tku - s * sku;
-      acc[6] += tkl + s * sku;
-      acc[7] += (1.0 - s) * sml + smu - tmu;
-      acc[8] += s * sml - tml;
-      acc[9] += tmu - s * smu;
-      acc[10] += tml + s * smu;
-    }
-    acc[1] *= a.m12;
-#pragma unroll
-    for (int k = 7; k < 11; ++k) acc[k] *= a.m12;
-  }
+  aug_cell<KK>(G, gl, a, p, ci, cj, threadIdx.x, blockDim.x, acc);
   block_sum_t<11>(acc, stage, outv);
   if (threadIdx.x < 11) partials[((long long)p * G.ncx * G.ncy + cj * G.ncx + ci) * 12 + threadIdx.x] = outv[threadIdx.x];
+}
+
+// One warp per T_H cell, 8 cells per block (cells of at most 32 x 32 fine nodes, where a
+// block per cell would give each thread a node or two and spend its time in the block
+// reduction); the sums are reduced by shuffles within the warp.
+template <int KK, bool PRE>
+__global__ void __launch_bounds__(256) k_aug_warp(DevGeom G, GlobalLayout gl, LevelArgs a, double* partials,
+                                                  RRPrefactor pf) {
+  extern __shared__ double aug_dyn[];
+  __shared__ int pflag;
+  const long long npre = PRE ? a.B : 0;
+  if (PRE && (long long)blockIdx.x < npre) {
+    const int p = blockIdx.x;
+    const long long band = (long long)pf.nhb * (pf.bw + 1);
+    rr_prefactor_block(pf.KH + p * band, pf.MH + p * band, a.lam + (long long)p * a.lam_stride, a.L, pf.nhb, pf.bw,
+                       pf.out + p * pf.stride, aug_dyn, &pflag);
+    return;
+  }
+  const int ncell = G.ncx * G.ncy;
+  const long long q = ((long long)blockIdx.x - npre) * 8 + (threadIdx.x >> 5);
+  if (q >= (long long)a.B * ncell) return;
+  const int lane = threadIdx.x & 31;
+  const int p = (int)(q / ncell), ci = (int)(q % ncell) % G.ncx, cj = (int)(q % ncell) / G.ncx;
+  double acc[11];
+  aug_cell<KK>(G, gl, a, p, ci, cj, lane, 32, acc);
+#pragma unroll
+  for (int k = 0; k < 11; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+  if (lane == 0) {
+    double* out = partials + ((long long)p * ncell + cj * G.ncx + ci) * 12;
+#pragma unroll
+    for (int k = 0; k < 11; ++k) out[k] = acc[k];
+  }
 }
 
 // u_out = c0 u~ + P_H c on level L, dense (ny+1) x (nx+1) per problem.
@@ -346,11 +387,25 @@ void launch_strip_update(const DevGeom& G, const GlobalLayout& gl, const LevelAr
 template <int KK>
 static void launch_aug_kk(const DevGeom& G, const GlobalLayout& gl, const LevelArgs& a, double* partials,
                           const RRPrefactor* pf, cudaStream_t s) {
+  const long long cells = (long long)a.B * G.ncx * G.ncy;
+  const bool warp = a.L <= 5;  // cells of at most 32 x 32 fine nodes
   if (!pf) {
-    k_aug<KK, false><<<(unsigned)((long long)a.B * G.ncx * G.ncy), 256, 0, s>>>(G, gl, a, partials, RRPrefactor{});
+    if (warp)
+      k_aug_warp<KK, false><<<(unsigned)((cells + 7) / 8), 256, 0, s>>>(G, gl, a, partials, RRPrefactor{});
+    else
+      k_aug<KK, false><<<(unsigned)cells, 256, 0, s>>>(G, gl, a, partials, RRPrefactor{});
     return;
   }
-  static bool attr = false;
+  static bool attr = false, attr_w = false;
+  if (warp) {
+    if (!attr_w) {
+      cudaFuncSetAttribute(k_aug_warp<KK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRRSmemMax);
+      attr_w = true;
+    }
+    const long long nb = (long long)a.B + (cells + 7) / 8;
+    k_aug_warp<KK, true><<<(unsigned)nb, 256, rr_prefactor_smem(pf->nhb, pf->bw), s>>>(G, gl, a, partials, *pf);
+    return;
+  }
   if (!attr) {
     cudaFuncSetAttribute(k_aug<KK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRRSmemMax);
     attr = true;

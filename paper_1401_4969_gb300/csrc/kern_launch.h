@@ -53,7 +53,7 @@ void launch_mg_tail(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, cons
 
 // ---- register-blocked fused multigrid, FP32 (kern_mgreg.cu); tiles of MLEV_RTILE_W x
 // MLEV_RTILE_H nodes; full = every grid of the tile list has no region mask ----
-bool rkernels_support(int kappa_kind, int pre, int post);
+bool rkernels_support(int kappa_kind, int pre, int post, double omega);
 // down: nu sweeps on depth d (x read from X, smoothed x written to XS), residual, restriction to
 // depth d + 1 (f and x = 0 there, in F and X)
 void launch_rdown(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F, int nu,

@@ -17,6 +17,9 @@
 //   up kernel reads XS and writes X): a box never reads values another block of the same
 //   launch writes, so results do not depend on the order in which blocks run.
 //
+// The smoother is plain red-black Gauss-Seidel (omega = 1; the shared-memory kernels serve
+// other relaxation factors).
+//
 // Node (i, j) of the box has colour (i + j) & 1 (0 red, 1 black) in its grid's coordinates;
 // the box origin is even in both directions, so the colour of register (q, k) (row q,
 // column k) is (q + k) & 1 and every register index below is known at compile time.
@@ -65,7 +68,7 @@ __device__ __forceinline__ void exchange_rows(float4 (*buf)[kRWarps][32], const 
 template <int KK, int C>
 __device__ __forceinline__ void rhalf_sweep(RegTile& x, const RegTile& f, unsigned mask, const float (&below)[4],
                                             const float (&above)[4], const KappaDev& kv, int p, int l, int gi0,
-                                            int gj0, float omega) {
+                                            int gj0) {
 #pragma unroll
   for (int q = 0; q < kRR; ++q) {
     const int k0 = (C ^ q) & 1;
@@ -81,14 +84,12 @@ __device__ __forceinline__ void rhalf_sweep(RegTile& x, const RegTile& f, unsign
       const float xe = k == 3 ? nb : x.v[q][k == 3 ? 3 : k + 1];
       const float xs = q == 0 ? below[k] : x.v[q == 0 ? 0 : q - 1][k];
       const float xn = q == kRR - 1 ? above[k] : x.v[q == kRR - 1 ? kRR - 1 : q + 1][k];
-      float nv;
+      float nv;  // plain Gauss-Seidel (omega = 1): the node takes the value that zeroes its residual
       if (KK == MLEV_KAPPA_ONE) {
-        const float s = f.v[q][k] + xe + xw + xn + xs;
-        nv = x.v[q][k] + omega * (s / 4.0f - x.v[q][k]);
+        nv = ((f.v[q][k] + xe) + (xw + xn) + xs) * 0.25f;
       } else {
         const EW<float> w = rweights<KK>(kv, p, l, gi0 + k, gj0 + q);
-        const float s = f.v[q][k] + w.e * xe + w.w * xw + w.n * xn + w.s * xs;
-        nv = x.v[q][k] + omega * (s / (w.e + w.w + w.n + w.s) - x.v[q][k]);
+        nv = ((f.v[q][k] + w.e * xe) + (w.w * xw + w.n * xn) + w.s * xs) / ((w.e + w.w) + (w.n + w.s));
       }
       if (mask & (1u << (q * 4 + k))) x.v[q][k] = nv;
     }
@@ -108,18 +109,29 @@ __device__ __forceinline__ void rload(RegTile& t, const float* base, int pitch, 
   }
 }
 
-// Unknown mask of the thread's 8 x 4 nodes: bit q * 4 + k.
+// Unknown mask of the thread's 8 x 4 nodes: bit q * 4 + k. On a grid with a region mask the
+// nodes are tested one by one only where some region cell next to the block is outside the
+// region (a node is an unknown when its four adjacent cells are in it; with region cells of
+// 4 or more nodes the block touches at most 3 x 3 of them, and inside the region interior
+// the bounds test alone decides).
 template <bool FULL>
 __device__ __forceinline__ unsigned rmask(const DevGeom& G, const GridDesc& g, int c0, int r0) {
+  bool inside = FULL || g.full;
+  if (!inside && g.rshift >= 2) {
+    const int ia = max(c0, 1), ib = min(c0 + 3, g.nx - 1), ja = max(r0, 1), jb = min(r0 + kRR - 1, g.ny - 1);
+    if (ia > ib || ja > jb) return 0u;
+    const int s = g.rshift;
+    inside = true;
+    for (int cy = (ja - 1) >> s; cy <= (jb >> s); ++cy)
+      for (int cx = (ia - 1) >> s; cx <= (ib >> s); ++cx) inside = inside && region_at(G, g, cx, cy);
+  }
   unsigned m = 0;
 #pragma unroll
   for (int q = 0; q < kRR; ++q)
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int i = c0 + k, j = r0 + q;
-      bool u;
-      if (FULL) u = i >= 1 && j >= 1 && i < g.nx && j < g.ny;
-      else u = is_unknown(G, g, i, j);
+      const bool u = inside ? (i >= 1 && j >= 1 && i < g.nx && j < g.ny) : is_unknown(G, g, i, j);
       if (u) m |= 1u << (q * 4 + k);
     }
   return m;
@@ -152,8 +164,7 @@ __device__ __forceinline__ RGrid rgrid(const GridDesc& g) {
 // to the next coarser grid (f_c = P^T r, x_c = 0) for the coarse nodes of the tile.
 template <int KK, int NU, bool FULL>
 __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restrict__ tiles, const float* __restrict__ X,
-                                                  float* XC, float* __restrict__ XS, float* F, float omega,
-                                                  int black_zero) {
+                                                  float* XC, float* __restrict__ XS, float* F, int black_zero) {
   __shared__ float4 xbuf[2][2][kRWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const Tile t = tiles[blockIdx.x];
@@ -176,9 +187,9 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
 #pragma unroll
   for (int s = 0; s < NU; ++s) {
     exchange_rows(xbuf[0], x, below, above, w, lane);
-    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0, omega);
+    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0);
     exchange_rows(xbuf[1], x, below, above, w, lane);
-    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0, omega);
+    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0);
   }
   rstore(x, XS + g.off, g.pitch, g.ny, c0, r0, t.y0, lane);
   // residual r = f - A x in f's registers (0 off the unknowns); with black_zero only the red
@@ -194,15 +205,18 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
       const float xe = k == 3 ? ex : x.v[q][k == 3 ? 3 : k + 1];
       const float xs = q == 0 ? below[k] : x.v[q == 0 ? 0 : q - 1][k];
       const float xn = q == kRR - 1 ? above[k] : x.v[q == kRR - 1 ? kRR - 1 : q + 1][k];
+      if (black_zero && ((q + k) & 1)) {  // black: zero after the closing black half-sweep
+        f.v[q][k] = 0.f;
+        continue;
+      }
       float r;
       if (KK == MLEV_KAPPA_ONE) {
-        r = f.v[q][k] - (4.0f * x.v[q][k] - xe - xw - xn - xs);
+        r = f.v[q][k] - (4.0f * x.v[q][k] - ((xe + xw) + (xn + xs)));
       } else {
         const EW<float> wt = rweights<KK>(G.kap, g.problem, g.level, gi0 + k, gj0 + q);
-        r = f.v[q][k] - ((wt.e + wt.w + wt.n + wt.s) * x.v[q][k] - wt.e * xe - wt.w * xw - wt.n * xn - wt.s * xs);
+        r = f.v[q][k] - (((wt.e + wt.w) + (wt.n + wt.s)) * x.v[q][k] - ((wt.e * xe + wt.w * xw) + (wt.n * xn + wt.s * xs)));
       }
-      const bool skip = black_zero && ((q + k) & 1);
-      f.v[q][k] = (!skip && (mask & (1u << (q * 4 + k)))) ? r : 0.f;
+      f.v[q][k] = (mask & (1u << (q * 4 + k))) ? r : 0.f;
     }
   }
   // restriction: coarse node (I, J) = fine (2I, 2J) = register (q, k), q even, k in {0, 2};
@@ -253,7 +267,7 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
 // post-smoothing), then NU red-black sweeps (black first). Reads x from XS, writes X.
 template <int KK, int NU, bool FULL>
 __global__ void __launch_bounds__(256, 2) k_rup(DevGeom G, const Tile* __restrict__ tiles, const float* __restrict__ XS,
-                                                float* X, const float* __restrict__ F, float omega, int red_only) {
+                                                float* X, const float* __restrict__ F, int red_only) {
   __shared__ float4 xbuf[2][2][kRWarps][32];
   __shared__ float xc[34][66];  // coarse nodes [by0/2, by0/2 + 33] x [bx0/2, bx0/2 + 65]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -303,34 +317,34 @@ __global__ void __launch_bounds__(256, 2) k_rup(DevGeom G, const Tile* __restric
 #pragma unroll
   for (int s = 0; s < NU; ++s) {  // two exchange buffers in turn: one barrier per half-sweep
     exchange_rows(xbuf[0], x, below, above, w, lane);
-    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0, omega);
+    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0);
     exchange_rows(xbuf[1], x, below, above, w, lane);
-    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0, omega);
+    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0);
   }
   rstore(x, X + g.off, g.pitch, g.ny, c0, r0, t.y0, lane);
 }
 
 // ------------------------------------------------------------------ launchers
-bool rkernels_support(int kappa_kind, int pre, int post) {
+bool rkernels_support(int kappa_kind, int pre, int post, double omega) {
   return (kappa_kind == MLEV_KAPPA_ONE || kappa_kind == MLEV_KAPPA_PER_COARSE_CELL) && pre >= 1 && pre <= 2 &&
-         post >= 1 && post <= 2;
+         post >= 1 && post <= 2 && omega == 1.0;
 }
 
 template <int KK, int NU>
 static void rdown_kk(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F,
                      double omega, int black_zero, cudaStream_t s) {
   if (full)
-    k_rdown<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, X, X, XS, F, (float)omega, black_zero);
+    k_rdown<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, X, X, XS, F, black_zero);
   else
-    k_rdown<KK, NU, false><<<n, 256, 0, s>>>(G, tiles, X, X, XS, F, (float)omega, black_zero);
+    k_rdown<KK, NU, false><<<n, 256, 0, s>>>(G, tiles, X, X, XS, F, black_zero);
 }
 template <int KK, int NU>
 static void rup_kk(const DevGeom& G, const Tile* tiles, int n, int full, const float* XS, float* X, const float* F,
                    double omega, int red_only, cudaStream_t s) {
   if (full)
-    k_rup<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, XS, X, F, (float)omega, red_only);
+    k_rup<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, XS, X, F, red_only);
   else
-    k_rup<KK, NU, false><<<n, 256, 0, s>>>(G, tiles, XS, X, F, (float)omega, red_only);
+    k_rup<KK, NU, false><<<n, 256, 0, s>>>(G, tiles, XS, X, F, red_only);
 }
 
 void launch_rdown(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F, int nu,
