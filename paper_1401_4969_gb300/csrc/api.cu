@@ -250,23 +250,25 @@ struct Launcher {
   // One V-cycle with the fused kernels: down (smooth + restrict) on the depths above the
   // tail, the tail (rest of the cycle in shared memory, one block per job), then up.
   // the register-blocked FP32 down / up kernels replace the shared-memory ones where they apply
+  // (per depth: the grids of a depth share one level, read from the depth's first tile)
   template <typename T>
-  bool use_reg(const std::vector<TileList>* rl) const {
-    return sizeof(T) == 4 && rl && rkernels_support(P.kappa_kind, o.pre_smooth, o.post_smooth, o.omega);
+  bool use_reg(const std::vector<TileList>* rl, int d) const {
+    if (sizeof(T) != 4 || !rl || (*rl)[d].count == 0) return false;
+    const int level = P.grids[P.tiles[(*rl)[d].off].grid].level;
+    return rkernels_support(P.kappa_kind, level, o.pre_smooth, o.post_smooth, o.omega);
   }
 
   template <typename T>
   void vcycle_fused(const std::vector<TileList>& fl, int dt, int D, const TileList& tail, size_t tail_smem, T* X, T* F,
                     bool direct, const std::vector<TileList>* rl = nullptr, const std::vector<int>* rfull = nullptr) {
     const double t = sizeof(T);
-    const bool reg = use_reg<T>(rl);
     float* XS = at<float>(ws, P.w_xs);
     for (int d = 0; d < dt; ++d) {
       if constexpr (sizeof(T) == 4) {
-        if (reg) {
+        if (use_reg<T>(rl, d)) {
           const TileList& tl = (*rl)[d];
           go(F_MG_DOWN, (3.5 * t + o.pre_smooth * kfine_extra()) * tl.unk, [&] {
-            launch_rdown(G, tiles_at(tl), tl.count, (*rfull)[d], X, XS, F, o.pre_smooth, o.omega, black_zero(), s);
+            launch_rdown(G, tiles_at(tl), tl.count, (*rfull)[d], X, XS, F, o.pre_smooth, black_zero(), s);
           });
           continue;
         }
@@ -292,10 +294,10 @@ struct Launcher {
     }
     for (int d = dt - 1; d >= 0; --d) {
       if constexpr (sizeof(T) == 4) {
-        if (reg) {
+        if (use_reg<T>(rl, d)) {
           const TileList& tl = (*rl)[d];
           go(F_MG_UP, (3.25 * t + o.post_smooth * kfine_extra()) * tl.unk, [&] {
-            launch_rup(G, tiles_at(tl), tl.count, (*rfull)[d], XS, X, F, o.post_smooth, o.omega, red_only(), s);
+            launch_rup(G, tiles_at(tl), tl.count, (*rfull)[d], XS, X, F, o.post_smooth, red_only(), s);
           });
           continue;
         }

@@ -53,14 +53,14 @@ void launch_mg_tail(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, cons
 
 // ---- register-blocked fused multigrid, FP32 (kern_mgreg.cu); tiles of MLEV_RTILE_W x
 // MLEV_RTILE_H nodes; full = every grid of the tile list has no region mask ----
-bool rkernels_support(int kappa_kind, int pre, int post, double omega);
+bool rkernels_support(int kappa_kind, int level, int pre, int post, double omega);  // per depth (grid level)
 // down: nu sweeps on depth d (x read from X, smoothed x written to XS), residual, restriction to
 // depth d + 1 (f and x = 0 there, in F and X)
 void launch_rdown(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F, int nu,
-                  double omega, int black_zero, cudaStream_t s);
+                  int black_zero, cudaStream_t s);
 // up: x = XS + P x_c (x_c from X at depth d + 1), nu sweeps, written to X
 void launch_rup(const DevGeom& G, const Tile* tiles, int n, int full, const float* XS, float* X, const float* F, int nu,
-                double omega, int red_only, cudaStream_t s);
+                int red_only, cudaStream_t s);
 // ---- global fields (kern_field.cu) ----
 struct LevelArgs {
   int L;                 // current level

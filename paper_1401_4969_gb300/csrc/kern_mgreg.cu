@@ -42,10 +42,61 @@ struct RegTile {
   float v[kRR][4];
 };
 
-// Coefficient weights of the stiffness row of node (gi, gj) (global lattice of level l).
+// Coefficient constant on each coarse cell (these kernels take it on levels l >= 3 only): the
+// columns gi0 - 1 .. gi0 + 3 and the rows gj0 - 1 .. gj0 + 7 a thread's stencils touch lie in
+// at most two coarse-cell columns X0, X0 + 1 and rows Y0, Y0 + 1 (a cell spans 2^l >= 8
+// nodes), so the thread loads those four values once; per node, bits select the cells NE, SE,
+// NW, SW of it (the cells of the lower coarse row / column have bit 0).
+struct CoarseK {
+  float k00, k10, k01, k11;  // k<x><y>: cell (X0 + x, Y0 + y), 0 outside the grid of cells
+  unsigned eb, wb;           // bit k: coarse column of gi0 + k (east cells) / of gi0 + k - 1 is X0 + 1
+  unsigned nb, sb;           // bit q: coarse row of gj0 + q (north cells) / of gj0 + q - 1 is Y0 + 1
+};
+
 template <int KK>
-__device__ __forceinline__ EW<float> rweights(const KappaDev& kv, int p, int l, int gi, int gj) {
-  return edge_weights_t<float, KK>(kv, p, l, gi, gj);
+__device__ __forceinline__ CoarseK make_coarse_k(const KappaDev& kv, int p, int l, int gi0, int gj0) {
+  CoarseK c{};
+  if (KK != MLEV_KAPPA_PER_COARSE_CELL) return c;
+  const int X0 = (gi0 - 1) >> l, Y0 = (gj0 - 1) >> l;
+  auto kap = [&](int X, int Y) {
+    if (X < 0 || Y < 0 || X >= kv.ncx || Y >= kv.ncy) return 0.f;
+    return kv.coarse_f[(long long)p * kv.ncx * kv.ncy + Y * kv.ncx + X];
+  };
+  c.k00 = kap(X0, Y0);
+  c.k10 = kap(X0 + 1, Y0);
+  c.k01 = kap(X0, Y0 + 1);
+  c.k11 = kap(X0 + 1, Y0 + 1);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (((gi0 + k) >> l) != X0) c.eb |= 1u << k;
+    if (((gi0 + k - 1) >> l) != X0) c.wb |= 1u << k;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (((gj0 + q) >> l) != Y0) c.nb |= 1u << q;
+    if (((gj0 + q - 1) >> l) != Y0) c.sb |= 1u << q;
+  }
+  return c;
+}
+
+// Coefficient weights of the stiffness row of register node (q, k) (global node (gi0 + k,
+// gj0 + q) of level l), with the same formulas as edge_weights_t.
+template <int KK>
+__device__ __forceinline__ EW<float> rweights(const KappaDev& kv, const CoarseK& c, int p, int l, int gi0, int gj0,
+                                              int q, int k) {
+  static_assert(KK == MLEV_KAPPA_ONE || KK == MLEV_KAPPA_PER_COARSE_CELL, "register kernels: kappa kinds");
+  {
+    const bool nh = (c.nb >> q) & 1u, sh = (c.sb >> q) & 1u, eh = (c.eb >> k) & 1u, wh = (c.wb >> k) & 1u;
+    const float kn0 = nh ? c.k01 : c.k00, kn1 = nh ? c.k11 : c.k10;
+    const float ks0 = sh ? c.k01 : c.k00, ks1 = sh ? c.k11 : c.k10;
+    const float kne = eh ? kn1 : kn0, knw = wh ? kn1 : kn0, kse = eh ? ks1 : ks0, ksw = wh ? ks1 : ks0;
+    EW<float> r;
+    r.e = 0.5f * (kne + kse);
+    r.n = 0.5f * (kne + knw);
+    r.w = 0.5f * (knw + ksw);
+    r.s = 0.5f * (kse + ksw);
+    return r;
+  }
 }
 
 // Row exchange between the warps of the block: buf[0][w] = first row of warp w, buf[1][w] =
@@ -65,10 +116,20 @@ __device__ __forceinline__ void exchange_rows(float4 (*buf)[kRWarps][32], const 
 
 // One red-black half-sweep of colour C over the thread's registers (C, the row parity and
 // the column are compile-time, so each row updates columns k0 and k0 + 2 with one shuffle).
+// The coefficient values are passed through an empty asm statement first: the compiler would
+// otherwise form the weights of all 32 nodes once and keep them live across the half-sweeps
+// (about 128 registers), which spills; recomputing them per node costs a few selects.
+__device__ __forceinline__ CoarseK opaque(CoarseK c) {
+  asm volatile("" : "+f"(c.k00), "+f"(c.k10), "+f"(c.k01), "+f"(c.k11), "+r"(c.eb), "+r"(c.wb), "+r"(c.nb),
+               "+r"(c.sb));
+  return c;
+}
+
 template <int KK, int C>
 __device__ __forceinline__ void rhalf_sweep(RegTile& x, const RegTile& f, unsigned mask, const float (&below)[4],
-                                            const float (&above)[4], const KappaDev& kv, int p, int l, int gi0,
-                                            int gj0) {
+                                            const float (&above)[4], const KappaDev& kv, const CoarseK& ck0, int p,
+                                            int l, int gi0, int gj0) {
+  const CoarseK ck = KK == MLEV_KAPPA_PER_COARSE_CELL ? opaque(ck0) : ck0;
 #pragma unroll
   for (int q = 0; q < kRR; ++q) {
     const int k0 = (C ^ q) & 1;
@@ -88,7 +149,7 @@ __device__ __forceinline__ void rhalf_sweep(RegTile& x, const RegTile& f, unsign
       if (KK == MLEV_KAPPA_ONE) {
         nv = ((f.v[q][k] + xe) + (xw + xn) + xs) * 0.25f;
       } else {
-        const EW<float> w = rweights<KK>(kv, p, l, gi0 + k, gj0 + q);
+        const EW<float> w = rweights<KK>(kv, ck, p, l, gi0, gj0, q, k);
         nv = ((f.v[q][k] + w.e * xe) + (w.w * xw + w.n * xn) + w.s * xs) / ((w.e + w.w) + (w.n + w.s));
       }
       if (mask & (1u << (q * 4 + k))) x.v[q][k] = nv;
@@ -163,8 +224,9 @@ __device__ __forceinline__ RGrid rgrid(const GridDesc& g) {
 // Down leg on one tile: NU red-black sweeps (red first), the residual, and its restriction
 // to the next coarser grid (f_c = P^T r, x_c = 0) for the coarse nodes of the tile.
 template <int KK, int NU, bool FULL>
-__global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restrict__ tiles, const float* __restrict__ X,
-                                                  float* XC, float* __restrict__ XS, float* F, int black_zero) {
+__global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restrict__ tiles,
+                                                  const float* __restrict__ X, float* XC, float* __restrict__ XS,
+                                                  float* F, int black_zero) {
   __shared__ float4 xbuf[2][2][kRWarps][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const Tile t = tiles[blockIdx.x];
@@ -183,18 +245,20 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
     for (int k = 0; k < 4; ++k)
       if (!(mask & (1u << (q * 4 + k)))) x.v[q][k] = 0.f;
   const int gi0 = g.ox + c0, gj0 = g.oy + r0;
+  const CoarseK ck = make_coarse_k<KK>(G.kap, g.problem, g.level, gi0, gj0);
   float below[4], above[4];
 #pragma unroll
   for (int s = 0; s < NU; ++s) {
     exchange_rows(xbuf[0], x, below, above, w, lane);
-    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0);
+    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
     exchange_rows(xbuf[1], x, below, above, w, lane);
-    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0);
+    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
   }
   rstore(x, XS + g.off, g.pitch, g.ny, c0, r0, t.y0, lane);
   // residual r = f - A x in f's registers (0 off the unknowns); with black_zero only the red
   // nodes (the black residuals vanish after the closing black half-sweep)
   exchange_rows(xbuf[0], x, below, above, w, lane);
+  const CoarseK ckr = KK == MLEV_KAPPA_PER_COARSE_CELL ? opaque(ck) : ck;
 #pragma unroll
   for (int q = 0; q < kRR; ++q) {
     const float wx = __shfl_up_sync(0xffffffffu, x.v[q][3], 1);
@@ -213,7 +277,7 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
       if (KK == MLEV_KAPPA_ONE) {
         r = f.v[q][k] - (4.0f * x.v[q][k] - ((xe + xw) + (xn + xs)));
       } else {
-        const EW<float> wt = rweights<KK>(G.kap, g.problem, g.level, gi0 + k, gj0 + q);
+        const EW<float> wt = rweights<KK>(G.kap, ckr, g.problem, g.level, gi0, gj0, q, k);
         r = f.v[q][k] - (((wt.e + wt.w) + (wt.n + wt.s)) * x.v[q][k] - ((wt.e * xe + wt.w * xw) + (wt.n * xn + wt.s * xs)));
       }
       f.v[q][k] = (mask & (1u << (q * 4 + k))) ? r : 0.f;
@@ -266,8 +330,9 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
 // red_only only the red nodes, since a plain Gauss-Seidel black half-sweep opens the
 // post-smoothing), then NU red-black sweeps (black first). Reads x from XS, writes X.
 template <int KK, int NU, bool FULL>
-__global__ void __launch_bounds__(256, 2) k_rup(DevGeom G, const Tile* __restrict__ tiles, const float* __restrict__ XS,
-                                                float* X, const float* __restrict__ F, int red_only) {
+__global__ void __launch_bounds__(256, 2) k_rup(DevGeom G, const Tile* __restrict__ tiles,
+                                                const float* __restrict__ XS, float* X, const float* __restrict__ F,
+                                                int red_only) {
   __shared__ float4 xbuf[2][2][kRWarps][32];
   __shared__ float xc[34][66];  // coarse nodes [by0/2, by0/2 + 33] x [bx0/2, bx0/2 + 65]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -313,26 +378,27 @@ __global__ void __launch_bounds__(256, 2) k_rup(DevGeom G, const Tile* __restric
       x.v[q][k] += v;
     }
   const int gi0 = g.ox + c0, gj0 = g.oy + r0;
+  const CoarseK ck = make_coarse_k<KK>(G.kap, g.problem, g.level, gi0, gj0);
   float below[4], above[4];
 #pragma unroll
   for (int s = 0; s < NU; ++s) {  // two exchange buffers in turn: one barrier per half-sweep
     exchange_rows(xbuf[0], x, below, above, w, lane);
-    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0);
+    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
     exchange_rows(xbuf[1], x, below, above, w, lane);
-    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, g.problem, g.level, gi0, gj0);
+    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
   }
   rstore(x, X + g.off, g.pitch, g.ny, c0, r0, t.y0, lane);
 }
 
 // ------------------------------------------------------------------ launchers
-bool rkernels_support(int kappa_kind, int pre, int post, double omega) {
-  return (kappa_kind == MLEV_KAPPA_ONE || kappa_kind == MLEV_KAPPA_PER_COARSE_CELL) && pre >= 1 && pre <= 2 &&
-         post >= 1 && post <= 2 && omega == 1.0;
+bool rkernels_support(int kappa_kind, int level, int pre, int post, double omega) {
+  return (kappa_kind == MLEV_KAPPA_ONE || (kappa_kind == MLEV_KAPPA_PER_COARSE_CELL && level >= 3)) && pre >= 1 &&
+         pre <= 2 && post >= 1 && post <= 2 && omega == 1.0;
 }
 
 template <int KK, int NU>
 static void rdown_kk(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F,
-                     double omega, int black_zero, cudaStream_t s) {
+                     int black_zero, cudaStream_t s) {
   if (full)
     k_rdown<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, X, X, XS, F, black_zero);
   else
@@ -340,7 +406,7 @@ static void rdown_kk(const DevGeom& G, const Tile* tiles, int n, int full, float
 }
 template <int KK, int NU>
 static void rup_kk(const DevGeom& G, const Tile* tiles, int n, int full, const float* XS, float* X, const float* F,
-                   double omega, int red_only, cudaStream_t s) {
+                   int red_only, cudaStream_t s) {
   if (full)
     k_rup<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, XS, X, F, red_only);
   else
@@ -348,25 +414,25 @@ static void rup_kk(const DevGeom& G, const Tile* tiles, int n, int full, const f
 }
 
 void launch_rdown(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F, int nu,
-                  double omega, int black_zero, cudaStream_t s) {
+                  int black_zero, cudaStream_t s) {
   if (!n) return;
   if (G.kap.kind == MLEV_KAPPA_ONE) {
-    if (nu == 1) rdown_kk<MLEV_KAPPA_ONE, 1>(G, tiles, n, full, X, XS, F, omega, black_zero, s);
-    else rdown_kk<MLEV_KAPPA_ONE, 2>(G, tiles, n, full, X, XS, F, omega, black_zero, s);
+    if (nu == 1) rdown_kk<MLEV_KAPPA_ONE, 1>(G, tiles, n, full, X, XS, F, black_zero, s);
+    else rdown_kk<MLEV_KAPPA_ONE, 2>(G, tiles, n, full, X, XS, F, black_zero, s);
   } else {
-    if (nu == 1) rdown_kk<MLEV_KAPPA_PER_COARSE_CELL, 1>(G, tiles, n, full, X, XS, F, omega, black_zero, s);
-    else rdown_kk<MLEV_KAPPA_PER_COARSE_CELL, 2>(G, tiles, n, full, X, XS, F, omega, black_zero, s);
+    if (nu == 1) rdown_kk<MLEV_KAPPA_PER_COARSE_CELL, 1>(G, tiles, n, full, X, XS, F, black_zero, s);
+    else rdown_kk<MLEV_KAPPA_PER_COARSE_CELL, 2>(G, tiles, n, full, X, XS, F, black_zero, s);
   }
 }
 void launch_rup(const DevGeom& G, const Tile* tiles, int n, int full, const float* XS, float* X, const float* F, int nu,
-                double omega, int red_only, cudaStream_t s) {
+                int red_only, cudaStream_t s) {
   if (!n) return;
   if (G.kap.kind == MLEV_KAPPA_ONE) {
-    if (nu == 1) rup_kk<MLEV_KAPPA_ONE, 1>(G, tiles, n, full, XS, X, F, omega, red_only, s);
-    else rup_kk<MLEV_KAPPA_ONE, 2>(G, tiles, n, full, XS, X, F, omega, red_only, s);
+    if (nu == 1) rup_kk<MLEV_KAPPA_ONE, 1>(G, tiles, n, full, XS, X, F, red_only, s);
+    else rup_kk<MLEV_KAPPA_ONE, 2>(G, tiles, n, full, XS, X, F, red_only, s);
   } else {
-    if (nu == 1) rup_kk<MLEV_KAPPA_PER_COARSE_CELL, 1>(G, tiles, n, full, XS, X, F, omega, red_only, s);
-    else rup_kk<MLEV_KAPPA_PER_COARSE_CELL, 2>(G, tiles, n, full, XS, X, F, omega, red_only, s);
+    if (nu == 1) rup_kk<MLEV_KAPPA_PER_COARSE_CELL, 1>(G, tiles, n, full, XS, X, F, red_only, s);
+    else rup_kk<MLEV_KAPPA_PER_COARSE_CELL, 2>(G, tiles, n, full, XS, X, F, red_only, s);
   }
 }
 
