@@ -55,6 +55,7 @@ extern "C" {
 #define MLEV_PREC_MIXED 1  /* FP32 multigrid for local/strip solves + FP64 residual refinement */
 
 #define MLEV_MAX_LEVELS 10
+#define MLEV_MAX_EIGENPAIRS 8
 
 typedef struct mlev_ctx mlev_ctx;
 
@@ -160,6 +161,23 @@ int mlev_set_levels(mlev_ctx* ctx, int n);
  * for PER_FINE_ELEM).
  */
 int mlev_set_forms(mlev_ctx* ctx, int batch, int kappa_kind, const double* kappa, int kappa_on_device);
+
+/*
+ * Number q of smallest eigenpairs to compute (default 1), 1 <= q <= MLEV_MAX_EIGENPAIRS.
+ * Section 4 states the correction step for one simple eigenvalue and says the version for
+ * several (and multiple) eigenvalues follows in the same way; Section 6 (Table 1) computes
+ * the first five. With q > 1 level 1 gives the q smallest eigenpairs of the pencil on
+ * V_{0h_1} (Algorithm 4.2 step 1), every correction step runs steps 1 and 2 of Algorithm 4.1
+ * for each pair with its own lambda_i, and step 3 is one Rayleigh-Ritz problem on
+ * V_{0H} + span{u~_1, ..., u~_q}; each u_i is b-normalised with b(u_i, W) > 0 for the T_H
+ * function W whose nodal value at the coarse node (X, Y) is 1 + frac(0.6180339887498949 k),
+ * k = Y (ncx + 1) + X (a positive, irregular weight). Outputs of mlev_solve / mlev_solve_host / mlev_solve_noalloc become
+ * lambda [batch][q] (ascending) and u [batch][q][grid]; mlev_report describes pair 1 of
+ * member 0. q > 1 needs a coefficient given on the host (kappa_on_device = 0), a coarse grid
+ * of at most 16 cells per side, and no gradient (mlev_grad_kappa returns MLEV_EUNSUPPORTED);
+ * otherwise MLEV_EUNSUPPORTED at the next solve. Call before mlev_workspace_size.
+ */
+int mlev_set_eigenpairs(mlev_ctx* ctx, int q);
 
 /* Bytes of device workspace mlev_solve needs for the current setup and opts. */
 int mlev_workspace_size(mlev_ctx* ctx, const mlev_opts* opts, size_t* bytes);

@@ -15,11 +15,15 @@ Reading used here (the paper gives no formulas for it):
   its q smallest Ritz pairs are (lambda_{i,h_{k+1}}, u_{i,h_{k+1}}), b-orthonormal.
   For a group of equal eigenvalues the span of the u~_i does not depend on the basis
   chosen for their eigenspace (steps 1 and 2 are linear in u for a fixed lambda).
-* Sign of each u_i (the paper fixes none): b(u_i, w) > 0 for the weight
-  w = 3 + s + t/2 + s t/3, with (s, t) the node's position scaled to [0, 1] over the grid's
-  bounding box. w > 0, so for the first eigenfunction (positive) this is the convention
-  int u > 0 of the one-eigenpair oracle; w is not orthogonal to the product modes
-  sin(k pi s) sin(l pi t), which the Laplacian's eigenfunctions on a square are.
+* Sign of each u_i (the paper fixes none): b(u_i, W) > 0 for the T_H function
+  W = sum_k omega_k phi_k over the free coarse nodes, omega at the coarse node (X, Y) being
+  1 + frac(0.6180339887498949 k) with k = Y (ncx + 1) + X (a fixed, positive, irregular
+  weight: a low-order polynomial weight is orthogonal to eigenfunctions that are odd under
+  a symmetry of the domain, for example sin(pi x) sin(3 pi y) - sin(3 pi x) sin(pi y) on the
+  square). W >= 0, so for the first eigenfunction (positive) this is the convention int u > 0
+  of the one-eigenpair oracle. (A T_H function makes b(u_i, W) a combination of the step-3
+  quantities P_H^T M u, which the Rayleigh-Ritz step has at hand.) Signs on the intermediate
+  levels do not change the result: steps 1 and 2 are linear in u.
 
 Every step is plain: sparse direct solves (SuperLU) for the local and G_{m+1} problems,
 dense scipy.linalg.eigh for both eigenproblems.
@@ -39,11 +43,14 @@ from . import multilevel as ML
 
 
 def sign_weight(hier: ML.Hierarchy, ell: int) -> np.ndarray:
-    """Nodal values of the sign weight w on level ell (all nodes)."""
-    lv = hier.levels[ell]
-    s = lv.pts[:, 0] / lv.nx
-    t = lv.pts[:, 1] / lv.ny
-    return 3.0 + s + 0.5 * t + s * t / 3.0
+    """Nodal values on level ell (all nodes) of the sign function W = sum of omega_k phi_k over
+    the free coarse nodes (the coarse hats embedded by exact interpolation)."""
+    c0 = hier.levels[0]
+    f = ML.free(hier, 0)
+    k = (c0.pts[f, 1] * (c0.nx + 1) + c0.pts[f, 0]).astype(np.float64)
+    x = k * 0.6180339887498949
+    omega = 1.0 + (x - np.floor(x))
+    return ML.coarse_basis(hier, ell) @ omega
 
 
 def normalize_columns(hier: ML.Hierarchy, ell: int, U: np.ndarray) -> np.ndarray:

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libmlev.so")
-SOURCES = ["plan.cpp", "kern_mg.cu", "kern_mgfused.cu", "kern_mgreg.cu", "kern_field.cu", "kern_eig.cu", "kern_adj.cu", "api.cu"]
+SOURCES = ["plan.cpp", "kern_mg.cu", "kern_mgfused.cu", "kern_mgreg.cu", "kern_multi.cu", "kern_field.cu", "kern_eig.cu", "kern_adj.cu", "api.cu"]
 HEADERS = ["mlev_internal.h", "plan.h", "kern_common.cuh", "kern_launch.h", "kern_blk.cuh", "kern_band.cuh",
            "kern_coarse.cuh", "kern_tail.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -452,8 +452,48 @@ struct Launcher {
     auto utL = [&](int l) { return ck_ut ? ck_ut + (size_t)(l - 1) * B * P.glay.bstride : ut[l & 1]; };
     auto cL = [&](int l) { return ck_c ? ck_c + (size_t)l * B * ncoef : c; };
     auto c0L = [&](int l) { return ck_c0 ? ck_c0 + (size_t)l * B : c0; };
+    // several eigenpairs: q virtual members per problem (kern_multi.cu)
+    const bool multi = P.q > 1;
+    SubEigArgs se{};
+    if (multi) {
+      se.q = P.q;
+      se.s = P.msub;
+      se.X = at<double>(ws, P.w_mX);
+      se.Y = at<double>(ws, P.w_mY);
+      se.AY = at<double>(ws, P.w_mAY);
+      se.BY = at<double>(ws, P.w_mBY);
+      se.theta = at<double>(ws, P.w_mth);
+      se.tol = 1e-10;
+      se.rtol = 1e-10;
+      se.res_slot = -1;
+      se.stat = stat;
+      se.stat_stride = stat_stride;
+    }
     // ---- Algorithm 4.2 step 1: eigenproblem on V_{0h_1}
-    {
+    if (multi) {
+      const int nx1 = P.lvl_nx(1);
+      double* K1 = at<double>(ws, P.w_mk1);
+      double* M1 = at<double>(ws, P.w_mm1);
+      go(F_BAND, 16.0 * P.Breal * P.m_nb1 * (nx1 + 1),
+         [&] { launch_band_level(G, P.Breal, P.q, 1, K1, M1, s); });
+      SubEigArgs a1 = se;
+      a1.nb = P.m_nb1;
+      a1.bwk = nx1 - 1;
+      a1.bwm = nx1;
+      a1.nbord = 0;
+      a1.K = K1;
+      a1.M = M1;
+      a1.kstride = a1.mstride = (long long)P.m_nb1 * (nx1 + 1);
+      a1.max_iter = std::max(o.level1_max_iter, 100);
+      a1.init_border = 0;
+      a1.it_slot = MLEV_STAT_L1_IT;
+      a1.res_slot = MLEV_STAT_L1_RES;
+      a1.noconv_flag = MLEV_ST_LEVEL1_NOCONV;
+      go(F_LEVEL1, 0.0, [&] { launch_sub_eig(G, a1, P.Breal, s); });
+      go(F_LEVEL1, 0.0, [&] {
+        launch_level1_multi_out(G, P.glay, P.Breal, P.q, P.msub, a1.X, a1.theta, utL(1), lam, n + 1, cL(1), c0L(1), s);
+      });
+    } else {
       Level1Args a{};
       a.B = B;
       a.grid_begin = P.l1_grid_begin;
@@ -505,6 +545,16 @@ struct Launcher {
         a.m12 = h * h / 12.0;
       }
       a.ut_prev = utL(L - 1);
+      if (multi && L >= 3) {
+        // u_{i,h_{L-1}} = sum_j D_ij u~_j + P_H c_i: the u~ combination into the buffer that
+        // level L's glue fills afterwards (only the embedding reads ut_prev before that)
+        double* comb = ut[L & 1];
+        const double* Dm = at<double>(ws, P.w_mD);
+        const double* src = utL(L - 1);
+        go(F_INTERP, 16.0 * B * P.lvl_nx(L - 1) * P.lvl_ny(L - 1),
+           [&] { launch_combine(P.glay, L - 1, P.Breal, P.q, Dm, src, comb, s); });
+        a.ut_prev = comb;
+      }
       a.ut = utL(L);
       a.uin = uin;
       a.r = r;
@@ -592,14 +642,56 @@ struct Launcher {
            [&] { launch_strip_update(G, P.glay, a, tiles_at(stop), stop.count, E, mixed ? 1 : 0, E32, s); });
       }
       // step 3: Rayleigh-Ritz on V_{0H} + span{u~}
+      if (multi) rr.use_pre = 0;
       go(F_AUG, (8.0 + kfine_extra()) * nfree,
          [&] { launch_aug(G, P.glay, a, partials, rr.use_pre ? &pf : nullptr, s); });
-      go(F_RR, 0.0, [&] { launch_rr(G, rr, s); });
+      if (multi) {  // ... + span{u~_1 .. u~_q}: Gram matrices, bordered pencil, subspace iteration
+        double* cross = at<double>(ws, P.w_mcross);
+        SubEigArgs ar = se;
+        ar.nb = P.nhb;
+        ar.bwk = P.bw - 1;
+        ar.bwm = P.bw;
+        ar.nbord = P.q;
+        ar.K = KH;
+        ar.M = MH;
+        ar.kstride = ar.mstride = (long long)P.q * P.nhb * (P.bw + 1);
+        ar.Ga = at<double>(ws, P.w_mGa);
+        ar.Gb = at<double>(ws, P.w_mGb);
+        ar.Aq = at<double>(ws, P.w_mAq);
+        ar.Bq = at<double>(ws, P.w_mBq);
+        ar.Z = at<double>(ws, P.w_mZ);
+        ar.max_iter = std::max(o.rr_max_iter, 50);
+        ar.init_border = 1;
+        ar.it_slot = MLEV_STAT_RR_IT + L;
+        ar.noconv_flag = MLEV_ST_RR_NOCONV;
+        const int npq = P.q * (P.q + 1) / 2;
+        go(F_AUG, 16.0 * nfree * npq / P.q, [&] { launch_cross_gram(G, P.glay, L, P.Breal, P.q, utL(L), cross, s); });
+        go(F_RR, 0.0, [&] {
+          launch_border_prep(G, P.Breal, P.q, partials, cross, at<double>(ws, P.w_mGa), at<double>(ws, P.w_mGb),
+                             at<double>(ws, P.w_mAq), at<double>(ws, P.w_mBq), s);
+        });
+        go(F_RR, 0.0, [&] { launch_sub_eig(G, ar, P.Breal, s); });
+        go(F_RR, 0.0, [&] {
+          launch_rr_multi_out(G, P.Breal, P.q, P.msub, P.nhb, P.bw, L, n + 1, ar.X, ar.theta, MH, ar.mstride, ar.Gb,
+                              cL(L), c0L(L), at<double>(ws, P.w_mD), lam, s);
+        });
+      } else {
+        go(F_RR, 0.0, [&] { launch_rr(G, rr, s); });
+      }
     }
     go(F_OUT, 16.0 * B, [&] { launch_lambda_out(B, n, lam, lambda_out, s); });
-    if (u_out)
+    if (u_out) {
+      const double* ufield = utL(n);
+      if (multi) {  // u_{i,h_n} = sum_j D_ij u~_j + P_H c_i
+        double* comb = ut[(n + 1) & 1];
+        const double* Dm = at<double>(ws, P.w_mD);
+        go(F_OUT, 16.0 * B * P.lvl_nx(n) * P.lvl_ny(n),
+           [&] { launch_combine(P.glay, n, P.Breal, P.q, Dm, utL(n), comb, s); });
+        ufield = comb;
+      }
       go(F_OUT, 16.0 * B * (P.lvl_nx(n) + 1) * (P.lvl_ny(n) + 1),
-         [&] { launch_output_u(G, P.glay, n, B, utL(n), cL(n), c0L(n), u_out, s); });
+         [&] { launch_output_u(G, P.glay, n, B, ufield, cL(n), c0L(n), u_out, s); });
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
     return MLEV_OK;
@@ -878,9 +970,18 @@ int upload_tables(mlev_ctx* ctx, void* ws, cudaStream_t s, bool force) {
   ctx->io_h2d += (long long)host.size();
   if (!P.kappa_on_device && !P.kappa_host.empty()) {
     const double* ksrc = P.kappa_host.data();
+    std::vector<double> krep;
+    if (P.q > 1) {  // one copy per virtual member b q + i
+      const size_t per = P.kappa_host.size() / (size_t)P.Breal;
+      krep.resize(per * (size_t)P.B);
+      for (int b = 0; b < P.Breal; ++b)
+        for (int i = 0; i < P.q; ++i)
+          std::memcpy(krep.data() + ((size_t)b * P.q + i) * per, P.kappa_host.data() + (size_t)b * per, per * 8);
+      ksrc = krep.data();
+    }
     std::vector<double> knan;
     if (fault_armed("kappa_nan")) {  // first positive value (a cell or triangle of Omega) -> NaN
-      knan = P.kappa_host;
+      knan.assign(ksrc, ksrc + (P.kappa_host.size() / (size_t)P.Breal) * (size_t)P.B);
       for (double& v : knan)
         if (v > 0) {
           v = std::nan("");
@@ -888,8 +989,9 @@ int upload_tables(mlev_ctx* ctx, void* ws, cudaStream_t s, bool force) {
         }
       ksrc = knan.data();
     }
-    CK(cudaMemcpyAsync(at<char>(ws, P.w_kstage), ksrc, P.kappa_host.size() * 8, cudaMemcpyHostToDevice, s));
-    ctx->io_h2d += (long long)P.kappa_host.size() * 8;
+    const size_t kbytes = (P.kappa_host.size() / (size_t)P.Breal) * (size_t)P.B * 8;
+    CK(cudaMemcpyAsync(at<char>(ws, P.w_kstage), ksrc, kbytes, cudaMemcpyHostToDevice, s));
+    ctx->io_h2d += (long long)kbytes;
   }
   CK(cudaStreamSynchronize(s));
   ctx->uploaded_ws = ws;
@@ -1167,6 +1269,18 @@ int mlev_set_levels(mlev_ctx* ctx, int n) {
   MLEV_CATCH(ctx)
 }
 
+int mlev_set_eigenpairs(mlev_ctx* ctx, int q) {
+  MLEV_TRY
+  if (!ctx) return MLEV_EINVAL;
+  if (q < 1 || q > MLEV_MAX_EIGENPAIRS) return fail(ctx, MLEV_EINVAL, "eigenpairs: need 1 <= q <= MLEV_MAX_EIGENPAIRS");
+  Plan& P = ctx->plan;
+  P.q = q;
+  P.B = P.Breal * q;
+  ctx->version++;
+  return MLEV_OK;
+  MLEV_CATCH(ctx)
+}
+
 int mlev_set_forms(mlev_ctx* ctx, int batch, int kappa_kind, const double* kappa, int kappa_on_device) {
   MLEV_TRY
   if (!ctx) return MLEV_EINVAL;
@@ -1178,7 +1292,8 @@ int mlev_set_forms(mlev_ctx* ctx, int batch, int kappa_kind, const double* kappa
   if (!P.has_domain) return fail(ctx, MLEV_ESTATE, "set the domain first");
   if (kappa_kind == MLEV_KAPPA_PER_FINE_ELEM && !P.has_levels)
     return fail(ctx, MLEV_ESTATE, "set the levels before per-element kappa");
-  P.B = batch;
+  P.Breal = batch;
+  P.B = batch * P.q;
   P.kappa_kind = kappa_kind;
   P.kappa_on_device = kappa_on_device != 0;
   P.kappa_dev = P.kappa_on_device ? kappa : nullptr;
@@ -1256,6 +1371,8 @@ int mlev_solve_host(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_
   rc = upload_tables(ctx, workspace, s, true);
   if (rc) return rc;
   const double* ksrc = kappa_device_src(ctx, workspace);
+  if (kappa_host && P.kappa_kind != MLEV_KAPPA_ONE && P.q > 1)
+    return fail(ctx, MLEV_EUNSUPPORTED, "new kappa values per call are not supported with several eigenpairs");
   if (kappa_host && P.kappa_kind != MLEV_KAPPA_ONE) {
     CK(cudaMemcpyAsync(at<char>(workspace, P.w_kstage), kappa_host, P.w_kstage.bytes, cudaMemcpyHostToDevice, s));
     ctx->io_h2d += (long long)P.w_kstage.bytes;
@@ -1298,6 +1415,7 @@ int mlev_grad_kappa(mlev_ctx* ctx, const mlev_opts* opts, void* workspace, size_
   if (ws_bytes < P.ws_grad_bytes)
     return fail(ctx, MLEV_ENOMEM, "workspace too small for the adjoint: need " + std::to_string(P.ws_grad_bytes) +
                                       " bytes (mlev_grad_workspace_size)");
+  if (P.q > 1) return fail(ctx, MLEV_EUNSUPPORTED, "the gradient is implemented for one eigenpair");
   if (!dlambda || !dkappa) return fail(ctx, MLEV_EINVAL, "dlambda and dkappa are required");
   if (layout != MLEV_GRAD_FINE_ELEM && layout != MLEV_GRAD_COARSE_CELL)
     return fail(ctx, MLEV_EINVAL, "unknown gradient layout");

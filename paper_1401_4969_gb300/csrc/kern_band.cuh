@@ -79,8 +79,8 @@ __device__ __forceinline__ void band_fwd(const double* Lb, const double* invD, d
 // needs npair <= blockDim.x). The pivots' reciprocals are the fast approximate ones: the
 // factors only precondition FP64 iterative refinement. Returns false (to all threads) on a
 // non-positive pivot.
-__device__ inline bool band_ldlt_f(float* Lb, float* invD, const int* pairs, int npair, int N, int bw) {
-  const int bw1 = bw + 1;
+__device__ inline bool band_ldlt_f(float* Lb, float* invD, const int* pairs, int npair, int N, int bw, int ls = 0) {
+  const int bw1 = ls > 0 ? ls : bw + 1;  // row stride (>= bw + 1)
   const bool mine = threadIdx.x < npair;
   const int aa = mine ? pairs[threadIdx.x] >> 16 : 0, bb = mine ? pairs[threadIdx.x] & 0xffff : 0;
   __syncthreads();

@@ -61,6 +61,48 @@ void launch_rdown(const DevGeom& G, const Tile* tiles, int n, int full, float* X
 // up: x = XS + P x_c (x_c from X at depth d + 1), nu sweeps, written to X
 void launch_rup(const DevGeom& G, const Tile* tiles, int n, int full, const float* XS, float* X, const float* F, int nu,
                 int red_only, cudaStream_t s);
+// ---- several eigenpairs (kern_multi.cu): q virtual batch members per problem ----
+constexpr int kSubEigSmemMax = MLEV_SUBEIG_SMEM_MAX;
+struct SubEigArgs {
+  int q, s;                 // eigenpairs wanted, block size (q <= s <= 16)
+  int nb, bwk, bwm;         // band rows; half bandwidth of K (factored, <= 31) and of the band storage
+  int nbord;                // border size: 0 (level 1) or q (Rayleigh-Ritz on V_{0H} + span{u~_i})
+  const double* K;          // [Breal] bands [nb][bwm + 1] (entry [r][d] = A(r, r - d)), stride kstride
+  const double* M;
+  long long kstride, mstride;
+  const double* Ga;         // [Breal][nbord][nb] border columns of A and B
+  const double* Gb;
+  const double* Aq;         // [Breal][nbord][nbord]
+  const double* Bq;
+  double* X;                // [Breal][s][nb + nbord]: out, B-orthonormal Ritz vectors (ascending)
+  double* Y;
+  double* AY;
+  double* BY;
+  double* Z;                // [Breal][nbord][nb]
+  double* theta;            // [Breal][s]: out, Ritz values
+  int max_iter;
+  double tol;               // FP64 Rayleigh-Ritz from the step the q wanted Ritz values change by <= tol
+  double rtol;              // stop when every wanted Ritz pair has ||A x - theta B x|| <= rtol ||theta B x||
+  int init_border;          // 1: start from the border unit vectors
+  long long* stat;          // per virtual member b q + i
+  int stat_stride, it_slot;
+  int res_slot;             // stat slot for the final relative residual (as double bits), or -1
+  int noconv_flag;
+};
+void launch_band_level(const DevGeom& G, int Breal, int q, int l, double* K, double* M, cudaStream_t s);
+void launch_cross_gram(const DevGeom& G, const GlobalLayout& gl, int L, int Breal, int q, const double* ut, double* out,
+                       cudaStream_t s);
+void launch_border_prep(const DevGeom& G, int Breal, int q, const double* partials, const double* cross, double* Ga,
+                        double* Gb, double* Aq, double* Bq, cudaStream_t s);
+void launch_sub_eig(const DevGeom& G, const SubEigArgs& a, int Breal, cudaStream_t s);
+void launch_level1_multi_out(const DevGeom& G, const GlobalLayout& gl, int Breal, int q, int s_, const double* X,
+                             const double* theta, double* ut1, double* lam, int lam_stride, double* c, double* c0,
+                             cudaStream_t s);
+void launch_rr_multi_out(const DevGeom& G, int Breal, int q, int s_, int nb, int bw, int L, int lam_stride,
+                         const double* X, const double* theta, const double* MH, long long mstride, const double* Gb,
+                         double* c, double* c0, double* D, double* lam, cudaStream_t s);
+void launch_combine(const GlobalLayout& gl, int L, int Breal, int q, const double* D, const double* src, double* dst,
+                    cudaStream_t s);
 // ---- global fields (kern_field.cu) ----
 struct LevelArgs {
   int L;                 // current level

@@ -46,6 +46,7 @@ struct GridDesc {
 
 // Output tile of the register-blocked fused multigrid kernels (kern_mgreg.cu): 112 x 52
 // nodes, origins multiples of the tile size (even, and x a multiple of 4 for float4 rows).
+#define MLEV_SUBEIG_SMEM_MAX (220 * 1024)  // shared memory limit of the subspace eigensolver
 #define MLEV_RTILE_W 112
 #define MLEV_RTILE_H 52
 

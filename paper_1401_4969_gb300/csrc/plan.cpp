@@ -564,6 +564,38 @@ std::string Plan::build(const mlev_opts& o) {
   take(w_out_lam, (size_t)B * 8);
   take(w_out_u, (size_t)B * (lvl_nx(n) + 1) * (lvl_ny(n) + 1) * 8);
   take(w_cinv, sub_direct ? (size_t)B * m * nd_max * nd_max * tsize : 0);
+  // ---- several eigenpairs
+  msub = 0;
+  m_nb1 = 0;
+  if (q > 1) {
+    if (q > MLEV_MAX_EIGENPAIRS) return "q exceeds MLEV_MAX_EIGENPAIRS";
+    if (kappa_on_device) return "UNSUPPORTED: several eigenpairs need the coefficient given on the host";
+    const int nx1 = lvl_nx(1), ny1 = lvl_ny(1);
+    m_nb1 = (nx1 - 1) * (ny1 - 1);
+    msub = std::min(16, q + 4);
+    if (nx1 - 1 > 31 || ncx - 1 > 31)
+      return "UNSUPPORTED: several eigenpairs need at most 16 coarse cells per side";
+    if (sub_eig_smem_bytes(m_nb1, nx1 - 1, msub) > (size_t)MLEV_SUBEIG_SMEM_MAX ||
+        sub_eig_smem_bytes(nhb, bw - 1, msub) > (size_t)MLEV_SUBEIG_SMEM_MAX)
+      return "UNSUPPORTED: the level-1 band factor of several eigenpairs does not fit in shared memory";
+    const size_t Nmax = (size_t)std::max(m_nb1, nhb + q);
+    const size_t band1 = (size_t)Breal * m_nb1 * (nx1 + 1) * 8;
+    take(w_mk1, band1);
+    take(w_mm1, band1);
+    const size_t blk = (size_t)Breal * msub * Nmax * 8;
+    take(w_mX, blk);
+    take(w_mY, blk);
+    take(w_mAY, blk);
+    take(w_mBY, blk);
+    take(w_mZ, (size_t)Breal * q * nhb * 8);
+    take(w_mGa, (size_t)Breal * q * nhb * 8);
+    take(w_mGb, (size_t)Breal * q * nhb * 8);
+    take(w_mAq, (size_t)Breal * q * q * 8);
+    take(w_mBq, (size_t)Breal * q * q * 8);
+    take(w_mD, (size_t)Breal * q * q * 8);
+    take(w_mth, (size_t)Breal * msub * 8);
+    take(w_mcross, (size_t)Breal * ncx * ncy * (q * (q + 1) / 2) * 2 * 8);
+  }
   ws_bytes = cur;
   // ---- adjoint regions (only mlev_grad_kappa touches them) ----
   const size_t ncoef = (size_t)(ncx + 1) * (ncy + 1);

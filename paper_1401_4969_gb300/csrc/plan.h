@@ -62,7 +62,9 @@ struct Plan {
   double delta = 0;
   int glue_mode = 0;
   int n = 0;
-  int B = 0;
+  int B = 0;                               // batch members the kernels see: Breal * q
+  int Breal = 0;                           // problems of the caller's batch
+  int q = 1;                               // smallest eigenpairs per problem (virtual members b q + i)
   int kappa_kind = 0;
   std::vector<double> kappa_host;
   const double* kappa_dev = nullptr;
@@ -100,6 +102,10 @@ struct Plan {
   Span w_x, w_f, w_x64, w_aug, w_lam, w_c, w_c0, w_stat, w_jobnorm, w_chol, w_out_lam, w_out_u, w_cinv, w_tmaps;
   Span w_rrpre;  // Rayleigh-Ritz factors prepared ahead of a level (mixed precision only)
   Span w_xs;     // smoothed x of the register-blocked down kernels (FP32, same layout as w_x)
+  // several eigenpairs (q > 1): level-1 band pencil, subspace blocks, bordered pencil, D
+  int msub = 0;                            // block size of the subspace iteration
+  int m_nb1 = 0;                           // level-1 band rows
+  Span w_mk1, w_mm1, w_mX, w_mY, w_mAY, w_mBY, w_mZ, w_mGa, w_mGb, w_mAq, w_mBq, w_mD, w_mth, w_mcross;
   size_t ws_bytes = 0;
   size_t tables_bytes = 0;
   // adjoint (mlev_grad_kappa): extra regions after the solve's, up to ws_grad_bytes
@@ -117,6 +123,10 @@ struct Plan {
   int lvl_ny(int l) const { return glay.ny[l - MLEV_LMIN]; }
   int lvl_pitch(int l) const { return glay.pitch[l - MLEV_LMIN]; }
 };
+
+// Shared memory of the subspace eigensolver of several eigenpairs (kern_multi.cu) for a band
+// of nb rows, factored half bandwidth bwk and block size s.
+size_t sub_eig_smem_bytes(int nb, int bwk, int s);
 
 // Validation helpers used by the C ABI (return "" if fine).
 std::string check_partition(Plan& p);

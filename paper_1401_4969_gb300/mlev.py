@@ -26,7 +26,8 @@ MAX_LEVELS = 10
 EXPORTS = ["mlev_opts_default", "mlev_create", "mlev_destroy", "mlev_last_error", "mlev_set_domain",
            "mlev_set_partition", "mlev_set_levels", "mlev_set_forms", "mlev_workspace_size", "mlev_problem_info",
            "mlev_solve", "mlev_solve_host", "mlev_profile_read", "mlev_solve_noalloc", "mlev_grad_workspace_size",
-           "mlev_grad_kappa"]
+           "mlev_grad_kappa", "mlev_set_eigenpairs"]
+MAX_EIGENPAIRS = 8
 NOALLOC_WORKSPACE_BYTES = 32 << 20
 GRAD_FINE_ELEM, GRAD_COARSE_CELL = 0, 1
 
@@ -93,6 +94,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.mlev_set_partition.argtypes = [P, I, VP, VP, D, I]
     lib.mlev_set_levels.argtypes = [P, I]
     lib.mlev_set_forms.argtypes = [P, I, I, VP, I]
+    lib.mlev_set_eigenpairs.argtypes = [P, I]
     lib.mlev_workspace_size.argtypes = [P, C.POINTER(Opts), C.POINTER(SZ)]
     lib.mlev_problem_info.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
@@ -103,6 +105,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.mlev_grad_workspace_size.argtypes = [P, C.POINTER(Opts), C.POINTER(SZ)]
     lib.mlev_grad_kappa.argtypes = [P, C.POINTER(Opts), VP, SZ, VP, VP, I, VP, VP, C.POINTER(Report)]
     for name in ("mlev_create", "mlev_set_domain", "mlev_set_partition", "mlev_set_levels", "mlev_set_forms",
+                 "mlev_set_eigenpairs",
                  "mlev_workspace_size", "mlev_problem_info", "mlev_solve", "mlev_solve_host", "mlev_profile_read",
                  "mlev_solve_noalloc", "mlev_grad_workspace_size", "mlev_grad_kappa"):
         getattr(lib, name).restype = I
@@ -135,8 +138,10 @@ class Solver:
     x0, y0, H, cell_in, cell_owner, overlap, delta, levels, batch, kappa_kind, kappa.
     """
 
-    def __init__(self, problem, device: int = 0, kappa_device=None):
-        """device = -1 gives a planning-only context (set-up, validation, sizes; no solves)."""
+    def __init__(self, problem, device: int = 0, kappa_device=None, eigenpairs: int = 1):
+        """device = -1 gives a planning-only context (set-up, validation, sizes; no solves);
+        eigenpairs = q computes the q smallest eigenpairs of every problem (outputs gain a
+        dimension q after the batch one)."""
         import torch
 
         if device >= 0 and not torch.cuda.is_available():
@@ -166,6 +171,8 @@ class Solver:
         else:
             self._kappa = np.ascontiguousarray(p.kappa, dtype=np.float64)
             self._check(self.lib.mlev_set_forms(h, p.batch, p.kappa_kind, _ptr(self._kappa), 0))
+        self.q = int(eigenpairs)
+        self._check(self.lib.mlev_set_eigenpairs(h, self.q))
         self._ws = None
 
     def _check(self, rc: int):
@@ -215,8 +222,9 @@ class Solver:
         import torch
 
         dev = f"cuda:{self.device}"
-        lam = torch.empty(self.problem.batch, dtype=torch.float64, device=dev)
-        u = torch.empty((self.problem.batch, *self.grid_shape()), dtype=torch.float64, device=dev) if want_u else None
+        lead = (self.problem.batch,) if self.q == 1 else (self.problem.batch, self.q)
+        lam = torch.empty(lead, dtype=torch.float64, device=dev)
+        u = torch.empty((*lead, *self.grid_shape()), dtype=torch.float64, device=dev) if want_u else None
         return lam, u
 
     def solve_into(self, opts: Opts, lam, u=None, stream=None, report: bool = False):

@@ -1,0 +1,111 @@
+"""Several eigenpairs on the GPU (mlev_set_eigenpairs) against the oracle's subspace form
+(oracle/multiple.py) on the same seeded inputs.
+
+Bars as for one eigenpair: relative eigenvalue error <= 1e-10 (FP64 path) / 1e-8 (mixed), on
+every eigenpair and level-n value. Eigenvectors: where an eigenvalue is separated from its
+neighbours (relative gap > 1e-3) the vector is unique up to sign and the sign rule fixes it, so
+||u_gpu - u_oracle||_b <= 1e-6; inside a group of close eigenvalues (the pairs near 5 pi^2 and
+10 pi^2 on the square, split by the mesh) only the group's span is unique, so each GPU vector's
+b-distance to the oracle span of its group is checked instead. The GPU vectors are
+b-orthonormal. Every case's q stops at a gap of the spectrum.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import multilevel as ML
+from oracle import multiple as MU
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-8}
+# q never cuts a group of close eigenvalues (the pair near 10 pi^2 on the square is split by
+# only ~1e-8 relative, so its first member alone is not well defined): q = 6 on the squares
+CASES = {
+    "c1-q6": (lambda: W.config1(), 6),
+    "c2n4-q6": (lambda: W.config2(levels=4), 6),
+    "lshape-n3-q3": (lambda: W.lshape(levels=3, seed=7), 3),
+    "kappa-coarse-b2-q3": (lambda: W.kappa_coarse_batch(W.unit_square(8, 2, 3), batch=2, seed=4), 3),
+    "kappa-fine-n3-q2": (lambda: W.kappa_fine_elem(W.unit_square(8, 2, 3), seed=5), 2),
+    "single-subdomain-q4": (lambda: W.single_subdomain(4, 3), 4),
+}
+
+
+def opts_for(prec):
+    from paper_1401_4969_gb300 import mlev
+
+    if prec == 0:
+        return mlev.default_opts(precision=0, vcycles=6, refine_passes=2, strip_vcycles=6)
+    return mlev.default_opts(precision=1)
+
+
+def groups(lams, gap=1e-3):
+    """Index groups of eigenvalues closer than `gap` (relative) to a neighbour."""
+    out, cur = [], [0]
+    for i in range(1, len(lams)):
+        if (lams[i] - lams[i - 1]) <= gap * abs(lams[i]):
+            cur.append(i)
+        else:
+            out.append(cur)
+            cur = [i]
+    out.append(cur)
+    return out
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("name", list(CASES))
+def test_several_eigenpairs_against_oracle(name, prec):
+    from paper_1401_4969_gb300 import mlev
+
+    make, q = CASES[name]
+    p = make()
+    s = mlev.Solver(p, eigenpairs=q)
+    lam_t, u_t = s.alloc_outputs(want_u=True)
+    rep = s.solve_into(opts_for(prec), lam_t, u_t, report=True)
+    assert rep["status_flags"] == 0
+    lam, u = lam_t.cpu().numpy().reshape(p.batch, q), u_t.cpu().numpy().reshape(p.batch, q, *s.grid_shape())
+    s.close()
+    for b in range(p.batch):
+        h = ML.build(p, b=b)
+        ref = MU.solve_multi(p, q, b=b, hier=h)
+        nxt = MU.global_eigpairs(h, p.levels, q + 1)[0]  # the test case must not cut a group
+        assert nxt[q] - nxt[q - 1] > 1e-3 * nxt[q], (name, nxt)
+        rel = np.abs(lam[b] - ref.lams) / ref.lams
+        assert np.all(rel <= TOL[prec]), (name, prec, b, lam[b], ref.lams, rel)
+        if b == 0:
+            lv = np.array(rep["lambda_levels"])
+            assert np.all(np.abs(lv - ref.lam_levels[:, 0]) <= TOL[prec] * ref.lam_levels[:, 0]), (lv, ref.lam_levels)
+        lv_n = h.levels[p.levels]
+        key = lv_n.key(lv_n.pts)
+        Mn = h.M[p.levels]
+        G = np.stack([u[b, i].ravel()[key] for i in range(q)], axis=1)
+        R = np.stack([ref.u[i].ravel()[key] for i in range(q)], axis=1)
+        assert np.allclose(G.T @ (Mn @ G), np.eye(q), atol=1e-8), name
+        for grp in groups(ref.lams):
+            if len(grp) == 1:
+                i = grp[0]
+                d = G[:, i] - R[:, i]
+                assert np.sqrt(max(d @ (Mn @ d), 0.0)) <= 1e-6, (name, prec, b, i)
+            else:
+                Rg = R[:, grp]  # b-orthonormal basis of the oracle group span
+                for i in grp:
+                    g = G[:, i]
+                    d = g - Rg @ (Rg.T @ (Mn @ g))
+                    assert np.sqrt(max(d @ (Mn @ d), 0.0)) <= 1e-6, (name, prec, b, i, grp)
+
+
+def test_one_eigenpair_through_the_several_path_matches_the_single():
+    """q = 1 keeps the one-eigenpair kernels; q = 2 computes the first pair with the subspace
+    kernels: the first eigenvalue agrees at the mixed bar."""
+    from paper_1401_4969_gb300 import mlev
+
+    p = W.config1()
+    s1 = mlev.Solver(p)
+    lam1, _, _ = s1.solve(mlev.default_opts())
+    s2 = mlev.Solver(p, eigenpairs=2)
+    lam2, _, _ = s2.solve(mlev.default_opts())
+    ref = MU.solve_multi(p, 2)
+    assert abs(float(lam2.reshape(-1)[0]) - ref.lams[0]) <= 1e-8 * ref.lams[0]
+    assert abs(float(lam1[0]) - ML.solve(p).lam) <= 1e-8 * ML.solve(p).lam
+    s1.close()
+    s2.close()
