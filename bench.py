@@ -414,6 +414,30 @@ def gpu_leg(name, timer, args, device, peak, peak_kind, steps, warmup, with_fp64
     return leg
 
 
+def profile_solve(name, steps):
+    """A workload's mixed-precision solve with its stored schedule, kernels launched one by one:
+    one untimed solve, then `steps` more (the launches an ncu capture selects from)."""
+    import torch
+
+    import workloads as W
+    from paper_1401_4969_gb300 import mlev
+
+    p = W.CONFIGS[name]()
+    solver = mlev.Solver(p)
+    sched, src = schedule(name, p, mlev.PREC_MIXED, 0, solver)
+    o = make_opts(mlev, mlev.PREC_MIXED, sched, graph=0)
+    lam, _ = solver.alloc_outputs(want_u=False)
+    rep = solver.solve_into(o, lam, None, report=True)
+    for _ in range(steps):
+        solver.solve_into(o, lam, None)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": WORKLOADS[name], "schedule": sched, "schedule_source": src,
+                      "launches_per_solve": rep["kernel_launches"], "solves": 1 + steps,
+                      "lambda_member0": float(lam[0])}))
+    solver.close()
+    return 0
+
+
 def public(leg):
     return {k: v for k, v in leg.items() if not k.startswith("_")}
 
@@ -429,9 +453,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-legs", action="store_true", help="skip the L-shape and 256-problem workloads")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing (512x512 kappa workload)")
+    ap.add_argument("--profile-solve", metavar="WORKLOAD", choices=sorted(WORKLOADS),
+                    help="no timing: run --steps solves of one workload with its stored schedule, launched "
+                         "directly (for ncu launch lists and captures), and print lambda")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_solve:
+        return profile_solve(args.profile_solve, args.steps)
     args.warmup = max(args.warmup, 3)
 
     rank, local_rank, world = dist_env()
