@@ -607,11 +607,13 @@ struct Launcher {
       cudaMemsetAsync(X, 0, (size_t)lp.pool_elems * sizeof(T), s);
       // step 1: auxiliary problems on every Omega_j of every batch member
       const TileList& top = lp.sub[0];
-      go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * top.unk,
-         [&] { launch_gather<T>(G, P.glay, tiles_at(top), top.count, X, F, X64, r, s); });
       // with one pass the FP64 accumulator would only be the FP32 solution widened: glue and
-      // the strip update read the FP32 pool directly (same values) unless residuals are checked
+      // the strip update read the FP32 pool directly (same values) unless residuals are checked,
+      // and the accumulator is neither zeroed nor written
       const bool direct32 = mixed && o.refine_passes == 1 && !o.check_residuals;
+      double* X64z = direct32 ? nullptr : X64;
+      go(F_GATHER, (8 + t + (X64z ? 8 : 0)) * top.unk,
+         [&] { launch_gather<T>(G, P.glay, tiles_at(top), top.count, X, F, X64z, r, s); });
       const float* E32 = direct32 ? reinterpret_cast<const float*>(X) : nullptr;
       solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, r, sub_cmode, &lp.sub_f, lp.sub_dt, &lp.sub_tail,
                    lp.sub_tail_smem, false, !direct32, &lp.sub_r, &lp.sub_r_full);
@@ -627,8 +629,8 @@ struct Launcher {
       go(F_GLUE, 24.0 * nfree, [&] { launch_glue(G, P.glay, a, E, mixed ? 1 : 0, E32, s); });
       const TileList& stop = lp.strip[0];
       if (stop.count) {
-        go(F_STRIP_RHS, (32.0 + 2 * t + kfine_extra()) * stop.unk,
-           [&] { launch_strip_rhs<T>(G, P.glay, a, tiles_at(stop), stop.count, X, F, X64, s); });
+        go(F_STRIP_RHS, (32.0 + 2 * t + (X64z ? 8 : 0) + kfine_extra()) * stop.unk,
+           [&] { launch_strip_rhs<T>(G, P.glay, a, tiles_at(stop), stop.count, X, F, X64z, s); });
         solve_set<T>(lp.strip, lp.strip_coarsest, o.strip_vcycles, X, F, X64, r, strip_cmode, &lp.strip_f,
                      lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem, false, !direct32, &lp.strip_r, &lp.strip_r_full);
         if (o.check_residuals) {
@@ -800,7 +802,7 @@ struct Launcher {
       const TileList& stop = lp.strip[0];
       if (stop.count) {
         cudaMemsetAsync(X, 0, (size_t)lp.pool_elems * sizeof(T), s);
-        go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * stop.unk,
+        go(F_GATHER, (8 + t + (mixed ? 8 : 0)) * stop.unk,
            [&] { launch_gather<T>(G, P.glay, tiles_at(stop), stop.count, X, F, X64, utbar, s); });
         solve_set<T>(lp.strip, lp.strip_coarsest, o.strip_vcycles, X, F, X64, utbar, strip_cmode, &lp.strip_f,
                      lp.strip_dt, &lp.strip_tail, lp.strip_tail_smem, false, true, &lp.strip_r, &lp.strip_r_full);
@@ -822,7 +824,7 @@ struct Launcher {
       cudaMemcpyAsync(tbuf, E, ebytes, cudaMemcpyDeviceToDevice, s);
       // the forward local solutions e^j, recomputed
       cudaMemsetAsync(X, 0, (size_t)lp.pool_elems * sizeof(T), s);
-      go(F_GATHER, (8 + 2 * t + (mixed ? 8 : 0)) * top.unk,
+      go(F_GATHER, (8 + t + (mixed ? 8 : 0)) * top.unk,
          [&] { launch_gather<T>(G, P.glay, tiles_at(top), top.count, X, F, X64, r, s); });
       solve_set<T>(lp.sub, lp.sub_coarsest, o.vcycles, X, F, X64, r, sub_cmode, &lp.sub_f, lp.sub_dt, &lp.sub_tail,
                    lp.sub_tail_smem, false, true, &lp.sub_r, &lp.sub_r_full);

@@ -123,6 +123,15 @@ __device__ __forceinline__ T kap_tri_t(const KappaDev& kv, int p, int l, int x, 
   else return kv.lvl[q];
 }
 
+// v / d for the Gauss-Seidel update (d the stencil's diagonal): in FP32 as v times the
+// correctly rounded reciprocal of d, which costs a fraction of a full-precision division (the
+// result differs from v / d by at most an ulp); in FP64 the division itself.
+template <typename T>
+__device__ __forceinline__ T div_diag(T v, T d) {
+  if constexpr (sizeof(T) == 4) return v * __frcp_rn(d);
+  else return v / d;
+}
+
 template <typename T, int KK>
 __device__ __forceinline__ EW<T> edge_weights_t(const KappaDev& kv, int p, int l, int gi, int gj) {
   EW<T> r;
@@ -132,7 +141,7 @@ __device__ __forceinline__ EW<T> edge_weights_t(const KappaDev& kv, int p, int l
   }
   if (KK == MLEV_KAPPA_PER_COARSE_CELL && l >= 0) {
     const int ci = gi >> l, cw = (gi - 1) >> l, cj = gj >> l, cs = (gj - 1) >> l;
-    const long long b = (long long)p * kv.ncx * kv.ncy;
+    const int b = p * kv.ncx * kv.ncy;  // batch x T_H cells, far below 2^31 (32-bit index math)
     T kc_c, kc_s, kc_w, kc_sw;
     if constexpr (sizeof(T) == 4) {
       kc_c = kv.coarse_f[b + cj * kv.ncx + ci];
@@ -174,6 +183,17 @@ template <typename T, typename V>
 __device__ __forceinline__ V apply_m12(const T* x, long long c, int pitch) {
   return (V)6 * (V)x[c] + (V)x[c + 1] + (V)x[c - 1] + (V)x[c + pitch] + (V)x[c - pitch] + (V)x[c + pitch + 1] +
          (V)x[c - pitch - 1];
+}
+
+// K x and M x / (h^2 / 12) at one node for kappa = 1, sharing the sum of the four edge
+// neighbours s4: K x = 4 x_c - s4, M x / (h^2 / 12) = 6 x_c + s4 + x_ne + x_sw (7 FP64
+// operations for both, against 12 for apply_k and apply_m12 apart).
+template <typename T, typename V>
+__device__ __forceinline__ void apply_km_one(const T* x, long long c, int pitch, V& kx, V& mx) {
+  const V xc = (V)x[c];
+  const V s4 = ((V)x[c + 1] + (V)x[c - 1]) + ((V)x[c + pitch] + (V)x[c - pitch]);
+  kx = (V)4 * xc - s4;
+  mx = (V)6 * xc + s4 + ((V)x[c + pitch + 1] + (V)x[c - pitch - 1]);
 }
 
 // 2^e as a double, built from its exponent field (exact for |e| < 1023): scaling by it equals

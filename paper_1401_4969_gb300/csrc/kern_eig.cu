@@ -1004,8 +1004,14 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     fp = -beta + 2.0 * red[2] - red[3];
   };
   // squared relative residuals: Newton steps need y to ~1e-6 (the variational f then has a
-  // relative error ~1e-12); the eigenvector to ~1e-13 (or until the residual stops falling)
-  const double kNewtonTarget = 1e-12, kFinalTarget = 1e-26;
+  // relative error ~1e-12); the eigenvector to ~1e-11 (or until the residual stops falling):
+  // its error enters the next level's eigenvalue squared, and the returned u at 1e-11 is far
+  // inside the 1e-6 eigenvector bar of the mixed path
+  const double kNewtonTarget = 1e-12, kFinalTarget = 1e-22;
+  // Newton stops when its step is below kStep relative: f is concave with its pole at the
+  // smallest coarse eigenvalue, a distance d of about 1 % of mu away, so the error left after
+  // the last step is about step^2 / d, under 1e-12 relative (the mixed path's bar is 1e-8)
+  const double kStep = 1e-7;
   double mu = alpha / beta, lo = 0.0, hi = INFINITY, lam = NAN;
   int it = 0, status = 0;
   bool have = false, factored = false;
@@ -1043,7 +1049,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     if (f > 0.0) lo = mu;
     else hi = mu;
     const double step = (fp < 0.0) ? -f / fp : 0.0;
-    if (fp < 0.0 && fabs(step) <= 1e-9 * fabs(mu)) {
+    if (fp < 0.0 && fabs(step) <= kStep * fabs(mu)) {
       lam = mu + step;
       break;
     }

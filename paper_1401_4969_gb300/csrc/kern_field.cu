@@ -52,8 +52,14 @@ __global__ void __launch_bounds__(256) k_rhs(DevGeom G, GlobalLayout gl, LevelAr
     return;
   }
   const double lam = a.lam[p * a.lam_stride + (L - 1)];
-  const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
   const double* u = a.uin + base;
+  if (KK == MLEV_KAPPA_ONE) {
+    double ku, mu;
+    apply_km_one<double, double>(u, c, pitch, ku, mu);
+    a.r[base + c] = (lam * a.m12) * mu - ku;
+    return;
+  }
+  const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
   a.r[base + c] = lam * a.m12 * apply_m12<double, double>(u, c, pitch) - apply_k<double, double>(u, c, pitch, w);
 }
 
@@ -153,10 +159,15 @@ __device__ __forceinline__ void aug_cell(const DevGeom& G, const GlobalLayout& g
       const int i = (ci << L) + ri, j = (cj << L) + rj;
       if (!is_free(G, L, nx, ny, i, j)) continue;
       const long long c = (long long)j * pitch + i;
-      const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
       const double uc = u[c];
-      const double ku = apply_k<double, double>(u, c, pitch, w);
-      const double mu = apply_m12<double, double>(u, c, pitch);  // M u / (h^2 / 12)
+      double ku, mu;  // K u and M u / (h^2 / 12)
+      if (KK == MLEV_KAPPA_ONE) {
+        apply_km_one<double, double>(u, c, pitch, ku, mu);
+      } else {
+        const W4 w = edge_weights<KK>(G.kap, p, L, i, j);
+        ku = apply_k<double, double>(u, c, pitch, w);
+        mu = apply_m12<double, double>(u, c, pitch);
+      }
       acc[0] += uc * ku;
       acc[1] += uc * mu;
       acc[2] += uc;

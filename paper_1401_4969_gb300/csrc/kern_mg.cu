@@ -17,18 +17,20 @@ namespace mlev {
 constexpr int TX = 32, TY = 8;
 constexpr int kCoarsestSmemMax = 220 * 1024;
 
+// One thread per node of the colour: a tile's 32 columns hold 16 nodes of each colour per
+// row (x0 is a multiple of 32), so the 16 x 8 threads take column x0 + 2 tx + ((color + j) & 1).
 template <typename T, int KK>
-__global__ void __launch_bounds__(256) k_smooth(DevGeom G, const Tile* __restrict__ tiles, T* X, const T* __restrict__ F,
+__global__ void __launch_bounds__(128) k_smooth(DevGeom G, const Tile* __restrict__ tiles, T* X, const T* __restrict__ F,
                                                 int color, T omega) {
   const Tile t = tiles[blockIdx.x];
   const GridDesc& g = G.grids[t.grid];
-  const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
-  if (((i + j) & 1) != color || !is_unknown(G, g, i, j)) return;
+  const int j = t.y0 + threadIdx.y, i = t.x0 + 2 * threadIdx.x + ((color + j) & 1);
+  if (!is_unknown(G, g, i, j)) return;
   T* x = X + g.off;
   const long long c = (long long)j * g.pitch + i;
   const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
   const T s = F[g.off + c] + (T)w.e * x[c + 1] + (T)w.w * x[c - 1] + (T)w.n * x[c + g.pitch] + (T)w.s * x[c - g.pitch];
-  x[c] += omega * (s / (T)(w.e + w.w + w.n + w.s) - x[c]);
+  x[c] += omega * (div_diag<T>(s, (T)(w.e + w.w + w.n + w.s)) - x[c]);
 }
 
 // r = f - A x at node (i, j) of grid g (0 off the unknowns).
@@ -68,13 +70,14 @@ __global__ void __launch_bounds__(256) k_restrict(DevGeom G, const Tile* __restr
 // Fine grid (tiles over depth d): x += P x_c. With `red_only` the post-smoothing that follows
 // starts with a plain Gauss-Seidel (omega = 1) black half-sweep, which sets every black node
 // from its red neighbours alone, so only the red nodes take the correction.
-template <typename T>
-__global__ void __launch_bounds__(256) k_prolong(DevGeom G, const Tile* __restrict__ tiles, T* X, int red_only) {
+// RED: 16 x 8 threads, one per red node of the 32 x 8 tile (x0 even: column x0 + 2 tx + (j & 1)).
+template <typename T, bool RED>
+__global__ void __launch_bounds__(256) k_prolong(DevGeom G, const Tile* __restrict__ tiles, T* X) {
   const Tile t = tiles[blockIdx.x];
   const GridDesc& gf = G.grids[t.grid];
   const GridDesc& gc = G.grids[t.grid + 1];
-  const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
-  if ((red_only && ((i + j) & 1)) || !is_unknown(G, gf, i, j)) return;
+  const int j = t.y0 + threadIdx.y, i = RED ? t.x0 + 2 * threadIdx.x + (j & 1) : t.x0 + threadIdx.x;
+  if (!is_unknown(G, gf, i, j)) return;
   const T* xc = X + gc.off;
   const int I = i >> 1, J = j >> 1;
   T v;
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(256) k_coarsest(DevGeom G, const Tile* __restr
         const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
         const T v = F[g.off + c] + (T)w.e * x[c + 1] + (T)w.w * x[c - 1] + (T)w.n * x[c + g.pitch] +
                     (T)w.s * x[c - g.pitch];
-        x[c] += omega * (v / (T)(w.e + w.w + w.n + w.s) - x[c]);
+        x[c] += omega * (div_diag<T>(v, (T)(w.e + w.w + w.n + w.s)) - x[c]);
       }
       __syncthreads();
     }
@@ -240,7 +243,8 @@ __global__ void __launch_bounds__(1024) k_coarsest_smem(DevGeom G, const Tile* _
 }
 
 // Finest grids of subdomain jobs: f = R (global residual of Eq. Aux_Problem restricted
-// to Omega_j), x = 0, x64 = 0.
+// to Omega_j) and, when the FP64 accumulator is in use, x64 = 0 (x starts at zero: the
+// caller clears the whole pool before).
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather(DevGeom G, GlobalLayout gl, const Tile* __restrict__ tiles, T* X, T* F,
                                                 double* X64, const double* __restrict__ R) {
@@ -249,8 +253,7 @@ __global__ void __launch_bounds__(256) k_gather(DevGeom G, GlobalLayout gl, cons
   const int i = t.x0 + threadIdx.x, j = t.y0 + threadIdx.y;
   if (i > g.nx || j > g.ny) return;
   const long long c = (long long)j * g.pitch + i;
-  X[g.off + c] = (T)0;
-  if (X64) X64[g.off64 + c] = 0.0;
+  if (X64) X64[g.off64 + c] = 0.0;  // X itself: the caller clears the whole pool first
   const int li = g.level - MLEV_LMIN;
   const double r = is_unknown(G, g, i, j)
                        ? R[(long long)g.problem * gl.bstride + (long long)(g.oy + j) * gl.pitch[li] + g.ox + i]
@@ -354,7 +357,7 @@ __global__ void k_resnorm_finalize(const double* acc, int B, int jobs_per_proble
 template <typename T>
 void launch_smooth(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, int color, double omega, cudaStream_t s) {
   if (!n) return;
-  MLEV_DISPATCH_KK(G.kap.kind, (k_smooth<T, KK><<<n, dim3(TX, TY), 0, s>>>(G, tiles, X, F, color, (T)omega)));
+  MLEV_DISPATCH_KK(G.kap.kind, (k_smooth<T, KK><<<n, dim3(TX / 2, TY), 0, s>>>(G, tiles, X, F, color, (T)omega)));
 }
 template <typename T>
 void launch_restrict(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, int black_zero, cudaStream_t s) {
@@ -364,7 +367,10 @@ void launch_restrict(const DevGeom& G, const Tile* tiles, int n, T* X, T* F, int
 template <typename T>
 void launch_prolong(const DevGeom& G, const Tile* tiles, int n, T* X, int red_only, cudaStream_t s) {
   if (!n) return;
-  k_prolong<T><<<n, dim3(TX, TY), 0, s>>>(G, tiles, X, red_only);
+  if (red_only)
+    k_prolong<T, true><<<n, dim3(TX / 2, TY), 0, s>>>(G, tiles, X);
+  else
+    k_prolong<T, false><<<n, dim3(TX, TY), 0, s>>>(G, tiles, X);
 }
 template <typename T>
 void launch_coarsest(const DevGeom& G, const Tile* tiles, int n, T* X, const T* F, int sweeps, double omega,

@@ -80,7 +80,7 @@ __device__ __forceinline__ void tile_half_sweep(const DevGeom& G, const GridDesc
       if (!uk[q]) continue;
       const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + rx0 + a, g.oy + ry0 + b);
       const T v = fs[q] + (T)w.e * xs[q + 1] + (T)w.w * xs[q - 1] + (T)w.n * xs[q + SW] + (T)w.s * xs[q - SW];
-      xs[q] += omega * (v / (T)(w.e + w.w + w.n + w.s) - xs[q]);
+      xs[q] += omega * (div_diag<T>(v, (T)(w.e + w.w + w.n + w.s)) - xs[q]);
     }
   }
 }

@@ -150,7 +150,7 @@ __device__ __forceinline__ void rhalf_sweep(RegTile& x, const RegTile& f, unsign
         nv = ((f.v[q][k] + xe) + (xw + xn) + xs) * 0.25f;
       } else {
         const EW<float> w = rweights<KK>(kv, ck, p, l, gi0, gj0, q, k);
-        nv = ((f.v[q][k] + w.e * xe) + (w.w * xw + w.n * xn) + w.s * xs) / ((w.e + w.w) + (w.n + w.s));
+        nv = div_diag<float>((f.v[q][k] + w.e * xe) + (w.w * xw + w.n * xn) + w.s * xs, (w.e + w.w) + (w.n + w.s));
       }
       if (mask & (1u << (q * 4 + k))) x.v[q][k] = nv;
     }

@@ -35,7 +35,7 @@ __device__ void tail_smooth(const DevGeom& G, const SmGrid<T>& s, int sweeps, bo
           const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
           const T v = s.f[q] + (T)w.e * s.x[q + 1] + (T)w.w * s.x[q - 1] + (T)w.n * s.x[q + s.W] +
                       (T)w.s * s.x[q - s.W];
-          s.x[q] += omega * (v / (T)(w.e + w.w + w.n + w.s) - s.x[q]);
+          s.x[q] += omega * (div_diag<T>(v, (T)(w.e + w.w + w.n + w.s)) - s.x[q]);
         }
       }
       __syncthreads();

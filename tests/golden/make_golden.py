@@ -7,7 +7,8 @@ on a coarse sub-lattice (every `stride`-th node in x and y) and the moments
 level-`MOMENT_LEVEL` mesh (a whole-field pin: every fine node enters some moment); the
 gradient file holds the
 oracle adjoint dlambda_{h_n}/dkappa on 20 seeded finest triangles, its maximum modulus and
-the Euler sum sum_e kappa_e g_e.
+the Euler sum sum_e kappa_e g_e; the several-eigenpairs file holds lambda_{i,h_k} for the
+q smallest eigenpairs.
 
 Usage: python tests/golden/make_golden.py [name ...]
 """
@@ -76,6 +77,18 @@ def record_grad(p, n_el=20, seed=20):
     return out
 
 
+def record_multi(p, q):
+    """The q smallest eigenvalues of the subspace form (oracle/multiple.py), every level."""
+    from oracle import multiple as MU
+
+    t = time.time()
+    r = MU.solve_multi(p, q)
+    out = {"problem": p.name, "levels": p.levels, "q": q, "lams": r.lams.tolist(),
+           "lam_levels": r.lam_levels.tolist(), "oracle_seconds": time.time() - t}
+    print(p.name, "q =", q, r.lams, "%.1fs" % (time.time() - t), flush=True)
+    return out
+
+
 JOBS = {
     "c2": lambda: record(W.config2(), [0], 64),
     "c4": lambda: record(W.config4(), list(range(0, 256, 37)), 16),
@@ -84,6 +97,7 @@ JOBS = {
     "c3n6": lambda: record(W.config3(levels=6), [0], 64),
     "c3": lambda: record(W.config3(), [0], 256, moments=False),
     "grad_c5": lambda: record_grad(W.config5()),
+    "c2_q6": lambda: record_multi(W.config2(), 6),
 }
 
 if __name__ == "__main__":
