@@ -82,7 +82,11 @@ typedef struct mlev_opts {
                            tail for the small ones (see tail_nodes) */
   int tail_nodes;       /* largest grid (nodes) the in-block tail of a fused V-cycle takes on; 0 = as many
                            levels as fit in shared memory */
-  int reserved[2];
+  int reg_depths;       /* fused = 2 only: the first reg_depths depths (finest first) run the
+                           register-blocked fused down / up legs instead of one launch per operation,
+                           where those legs apply (FP32, plain Gauss-Seidel with omega = 1, 1 or 2
+                           sweeps, kappa = 1 or per coarse cell on levels >= 3); 0 = none */
+  int reserved;
 } mlev_opts;
 
 /* Per-solve diagnostics (batch member 0 unless noted). */

@@ -28,7 +28,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 TUNE_KEYS = ("vcycles", "refine_passes", "strip_vcycles", "pre_smooth", "post_smooth", "coarse_sweeps", "fused",
-             "tail_nodes", "level1_tol")
+             "tail_nodes", "reg_depths", "level1_tol")
 FLOAT_KEYS = ("level1_tol",)
 # A schedule is accepted when every eigenvalue is within SAFETY * target_rel of the reference
 # (a 4x margin to the target for what the reference itself and other inputs may add).
@@ -59,9 +59,9 @@ def problem_signature(problem) -> str:
 def cycle_candidates() -> list[dict]:
     """(vcycles, refine_passes, strip_vcycles) in increasing order of V-cycle work."""
     out = []
-    for vc in (1, 2, 3, 4, 6):
+    for vc in (1, 2, 3, 4, 5, 6, 8):
         for rp in (1, 2):
-            for svc in (1, 2, 3, 4, 6):
+            for svc in (1, 2, 3, 4, 6, 8):
                 if svc > vc + 2:
                     continue
                 out.append({"vcycles": vc, "refine_passes": rp, "strip_vcycles": svc})
@@ -93,13 +93,14 @@ class TuneResult:
 
 
 def search(evaluate, target_rel: float, safety: float = SAFETY, base: dict | None = None,
-           max_accept: int = 3) -> TuneResult:
+           max_accept: int = 3, reg_legs: bool = True) -> TuneResult:
     """Staged search with an evaluator evaluate(opts dict) -> (ms, max relative error).
 
     Stage 1 walks the cycle candidates in increasing work and stops after `max_accept`
     accepted schedules; stage 2 lowers the smoothing and coarsest sweeps of the fastest
     accepted one and loosens the level-1 residual target; stage 3 compares the fused and
-    unfused multigrid kernels."""
+    unfused multigrid kernels, and for the hybrid the register-blocked legs on its finest
+    one or two depths."""
     base = dict(base or {"pre_smooth": 2, "post_smooth": 2, "coarse_sweeps": 40, "fused": 1, "tail_nodes": 0,
                          "level1_tol": 1e-10})
     tol = safety * target_rel
@@ -134,6 +135,12 @@ def search(evaluate, target_rel: float, safety: float = SAFETY, base: dict | Non
         t = run({**best.opts, "fused": fused, "tail_nodes": tn})
         if t.ok and t.ms < best.ms:
             best = t
+    # the hybrid with the register-blocked legs (FP32 only) on its finest depths
+    if reg_legs and best.opts.get("fused") == 2:
+        for rd in (1, 2):
+            t = run({**best.opts, "reg_depths": rd})
+            if t.ok and t.ms < best.ms:
+                best = t
     return TuneResult(opts={k: best.opts[k] for k in TUNE_KEYS if k in best.opts}, ms=best.ms, err=best.err,
                       target_rel=target_rel, trials=trials)
 
@@ -200,7 +207,7 @@ def tune(problem, precision: int = 1, target_rel: float = 1e-8, device: int = 0,
             err = float(np.max(np.abs(lam.cpu().numpy() - lam_ref) / np.abs(lam_ref)))
             return e0.elapsed_time(e1) / reps, err
 
-        res = search(evaluate, target_rel)
+        res = search(evaluate, target_rel, reg_legs=precision == mlev.PREC_MIXED)
     finally:
         if own:
             s.close()

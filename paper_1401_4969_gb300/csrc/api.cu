@@ -111,14 +111,14 @@ bool opts_valid(const mlev_opts* o) {
          o->refine_passes >= 1 && o->strip_vcycles >= 1 && o->pre_smooth >= 0 && o->post_smooth >= 0 &&
          o->pre_smooth + o->post_smooth >= 1 && o->coarse_sweeps >= 1 && o->level1_max_iter >= 1 &&
          o->level1_tol > 0 && o->rr_max_iter >= 1 && o->omega > 0 && o->omega < 2 && o->tail_nodes >= 0 &&
-         o->fused >= 0 && o->fused <= 2;
+         o->fused >= 0 && o->fused <= 2 && o->reg_depths >= 0;
 }
 
 std::string opts_key(const mlev_opts* o) {
   char b[256];
-  snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%.17g/%d/%.17g/%d/%d/%d", o->precision, o->vcycles,
+  snprintf(b, sizeof b, "%d/%d/%d/%d/%d/%d/%d/%d/%.17g/%d/%.17g/%d/%d/%d/%d", o->precision, o->vcycles,
            o->refine_passes, o->strip_vcycles, o->pre_smooth, o->post_smooth, o->coarse_sweeps, o->level1_max_iter,
-           o->level1_tol, o->rr_max_iter, o->omega, o->check_residuals, o->fused, o->tail_nodes);
+           o->level1_tol, o->rr_max_iter, o->omega, o->check_residuals, o->fused, o->tail_nodes, o->reg_depths);
   return b;
 }
 
@@ -311,13 +311,31 @@ struct Launcher {
   // (large grids, many blocks), then the tail kernel for every coarser grid of the jobs.
   template <typename T>
   void vcycle_hybrid(const std::vector<TileList>& lists, int dt, int D, const TileList& tail, size_t tail_smem, T* X,
-                     T* F, bool direct) {
+                     T* F, bool direct, const std::vector<TileList>* rl = nullptr,
+                     const std::vector<int>* rfull = nullptr) {
     const double t = sizeof(T);
+    float* XS = at<float>(ws, P.w_xs);
     auto smooth = [&](int d, int color) {
       go(F_SMOOTH, (2 * t + 0.5 * kfine_extra()) * lists[d].unk,
          [&] { launch_smooth<T>(G, tiles_at(lists[d]), lists[d].count, X, F, color, o.omega, s); });
     };
+    // the first reg_depths depths: the register-blocked legs (pre-smoothing, residual and
+    // restriction in one launch; prolongation and post-smoothing in one), the per-operation
+    // kernels below them; both leave the coarse grid's x = 0 and f = P^T r
+    auto reg = [&](int d) {
+      if constexpr (sizeof(T) == 4) return d < o.reg_depths && rl && (int)rl->size() > d && use_reg<T>(rl, d);
+      return false;
+    };
     for (int d = 0; d < dt; ++d) {
+      if constexpr (sizeof(T) == 4) {
+        if (reg(d)) {
+          const TileList& tl = (*rl)[d];
+          go(F_MG_DOWN, (3.5 * t + o.pre_smooth * kfine_extra()) * tl.unk, [&] {
+            launch_rdown(G, tiles_at(tl), tl.count, (*rfull)[d], X, XS, F, o.pre_smooth, black_zero(), s);
+          });
+          continue;
+        }
+      }
       for (int k = 0; k < o.pre_smooth; ++k) {
         smooth(d, 0);
         smooth(d, 1);
@@ -338,6 +356,15 @@ struct Launcher {
       });
     }
     for (int d = dt - 1; d >= 0; --d) {
+      if constexpr (sizeof(T) == 4) {
+        if (reg(d)) {
+          const TileList& tl = (*rl)[d];
+          go(F_MG_UP, (3.25 * t + o.post_smooth * kfine_extra()) * tl.unk, [&] {
+            launch_rup(G, tiles_at(tl), tl.count, (*rfull)[d], XS, X, F, o.post_smooth, red_only(), s);
+          });
+          continue;
+        }
+      }
       go(F_PROLONG, 2.25 * t * lists[d].unk,
          [&] { launch_prolong<T>(G, tiles_at(lists[d]), lists[d].count, X, red_only(), s); });
       for (int k = 0; k < o.post_smooth; ++k) {
@@ -376,7 +403,7 @@ struct Launcher {
         if (fused)
           vcycle_fused<T>(*fl, dt, D, *tail, tail_smem, X, F, cmode == C_DIRECT, rl, rfull);
         else if (hybrid)
-          vcycle_hybrid<T>(lists, dt, D, *tail, tail_smem, X, F, cmode == C_DIRECT);
+          vcycle_hybrid<T>(lists, dt, D, *tail, tail_smem, X, F, cmode == C_DIRECT, rl, rfull);
         else
           vcycle<T>(lists, coarsest, X, F, cmode);
       }

@@ -38,7 +38,7 @@ class Opts(C.Structure):
                 ("coarse_sweeps", C.c_int), ("level1_max_iter", C.c_int), ("level1_tol", C.c_double),
                 ("rr_max_iter", C.c_int), ("use_graph", C.c_int), ("omega", C.c_double),
                 ("check_residuals", C.c_int), ("profile", C.c_int), ("fused", C.c_int), ("tail_nodes", C.c_int),
-                ("reserved", C.c_int * 2)]
+                ("reg_depths", C.c_int), ("reserved", C.c_int)]
 
 
 class KernelStat(C.Structure):
