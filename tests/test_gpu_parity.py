@@ -209,17 +209,19 @@ def test_fused_multigrid_matches_unfused(name, prec):
     s.close()
 
 
-@pytest.mark.parametrize("form", [(0, 0), (2, 4096), (2, 256), (1, 0)])
+@pytest.mark.parametrize("form", [(0, 0, 0), (2, 4096, 0), (2, 256, 0), (1, 0, 0), (2, 256, 1), (2, 256, 2)])
 @pytest.mark.parametrize("name", ["lshape-n4", "kappa-fine-n3", "kappa-coarse-b3", "c2n4"])
 def test_vcycle_forms_against_oracle(name, form):
     """Every V-cycle form (fused = 0: one launch per operation; 2: per-operation kernels above
-    tail_nodes and the one-block tail below; 1: fused down / up legs and the tail) meets the
-    mixed-precision bars against the oracle, not only against each other."""
+    tail_nodes and the one-block tail below, with the register-blocked legs on the first
+    reg_depths depths where they apply -- not for kappa per finest triangle; 1: fused down /
+    up legs and the tail) meets the mixed-precision bars against the oracle, not only
+    against each other."""
     from paper_1401_4969_gb300 import mlev
 
     p = CASES[name]()
-    fused, tail = form
-    lam, u, rep = _run(p, mlev.default_opts(precision=1, fused=fused, tail_nodes=tail))
+    fused, tail, reg = form
+    lam, u, rep = _run(p, mlev.default_opts(precision=1, fused=fused, tail_nodes=tail, reg_depths=reg))
     assert rep["status_flags"] == 0
     for b in range(p.batch):
         ref = ML.solve(p, b=b)
