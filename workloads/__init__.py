@@ -216,3 +216,35 @@ def config5(levels: int = 5, seed: int = 5) -> Problem:
 
 
 CONFIGS = {"c1": config1, "c2": config2, "c3": config3, "c4": config4, "c5": config5}
+
+
+# --- Example 2 of Section 6 (full tensor coefficient, weighted mass) ---------------------
+
+def example2_tensor(x, y):
+    """The coefficient matrix of Example 2 at (x, y): (a11, a12, a22) with a11 = exp(1 + x^2),
+    a12 = a21 = exp(x y), a22 = exp(1 + y^2)."""
+    return np.exp(1.0 + x * x), np.exp(x * y), np.exp(1.0 + y * y)
+
+
+def example2_weight(x, y):
+    """The weight of b(u, v) = (phi u, v) in Example 2: phi = (1 + x^2)(1 + y^2)."""
+    return (1.0 + x * x) * (1.0 + y * y)
+
+
+def example2(levels: int = 4, parts: int = 4) -> Problem:
+    """Example 2's domain and decomposition: (-1,1)^2, H = 0.1 (a 20 x 20 coarse grid),
+    delta = 0.1, parts x parts equal blocks D_j with overlap one coarse cell. The forms come
+    from example2_tensor and example2_weight (the GPU path takes kappa I and the plain mass)."""
+    nc = 20
+    H = 2.0 / nc
+    m = parts * parts
+    return Problem(
+        name=f"ex2-square20-m{m}-n{levels}",
+        ncx=nc, ncy=nc, x0=-1.0, y0=-1.0, H=H,
+        cell_in=np.ones((nc, nc), np.uint8),
+        cell_owner=_grid_owner(nc, nc, parts, parts),
+        overlap=np.full(m, 1, np.int32),
+        delta=H,
+        levels=levels,
+        notes={"forms": "example2"},
+    )
