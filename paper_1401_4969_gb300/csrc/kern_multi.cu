@@ -122,34 +122,73 @@ __global__ void k_combine(GlobalLayout gl, int L, int Breal, int q, const double
 
 namespace {
 
-// S x = b in place by one warp (any warp, its own vector y in shared memory), with FP32 factors
-// pre-scaled to L(i, i - d) = Ls[i * ls + d] and invD = 1 / D: the register-window scheme of
-// band_solve_shfl (entry e in lane e mod 32, one shuffle per step), needs bw <= 31. The step
-// is bound by the shuffle's latency (about 60 cycles a step with the loads; loads issued a
-// step ahead measured twice as slow); with ls even the lanes' coefficient loads
-// (j + d) ls + d = j ls + d (ls + 1) fall into distinct banks.
-__device__ void warp_band_solve(const float* Ls, int ls, const float* invD, float* y, int N, int bw) {
+// Blocked form of the FP32 band factor K = L D L^T (half bandwidth < 32): rows in blocks of
+// 32. Tile k (32 x 33 floats, row stride 33 so that a lane reading a row or a column of the
+// tile hits its own bank) holds T_k = L_kk^{-1} below the diagonal (unit diagonal implicit)
+// and the coupling C_k[i][m] = L(32 k + i, 32 (k - 1) + m) above it (nonzero only for m > i).
+constexpr int kTB = 32;
+constexpr int kTP = kTB + 1;
+constexpr int kTT = kTB * kTP;
+__host__ __device__ inline int sub_eig_nbk(int nb) { return (nb + kTB - 1) / kTB; }
+
+// K~^{-1} y in place by one warp: z_k = T_k (y_k - C_k z_{k-1}) block by block, then
+// x_k = T_k^T (D^{-1} z_k - C_{k+1}^T x_{k+1}) from the last block. Each block is two 32-term
+// products (shuffles and FMAs) instead of 32 dependent substitution steps. y has 32 nbk
+// entries, those past the last row zero.
+__device__ void warp_block_solve(const float* tiles, const float* invD, float* y, int nbk) {
   const int lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
-  float v = lane < N ? y[lane] : 0.f;
-  for (int j = 0; j < N; ++j) {
-    const int h = j & 31, d = (lane - j) & 31;
-    const float coef = (d >= 1 && d <= bw && j + d < N) ? Ls[(j + d) * ls + d] : 0.f;
-    const float refill = (j + 32 < N) ? y[j + 32] : 0.f;
-    const float dj = invD[j];
-    const float zj = __shfl_sync(full, v, h);
-    v = (lane == h) ? refill : v - coef * zj;
-    y[j] = zj * dj;
+  float zp = 0.f;
+  for (int k = 0; k < nbk; ++k) {
+    const float* Tr = tiles + (size_t)k * kTT + lane * kTP;  // row `lane` of tile k
+    float t = y[k * kTB + lane];
+    if (k > 0) {
+      float t1 = 0.f;
+#pragma unroll
+      for (int m = 0; m < kTB; m += 2) {
+        const float z0 = __shfl_sync(full, zp, m), z1 = __shfl_sync(full, zp, m + 1);
+        t -= (m > lane ? Tr[m] : 0.f) * z0;
+        t1 -= (m + 1 > lane ? Tr[m + 1] : 0.f) * z1;
+      }
+      t += t1;
+    }
+    float z = t, z1 = 0.f;
+#pragma unroll
+    for (int m = 0; m < kTB; m += 2) {
+      const float t0 = __shfl_sync(full, t, m), tt = __shfl_sync(full, t, m + 1);
+      z += (m < lane ? Tr[m] : 0.f) * t0;
+      z1 += (m + 1 < lane ? Tr[m + 1] : 0.f) * tt;
+    }
+    z += z1;
+    y[k * kTB + lane] = z * invD[k * kTB + lane];
+    zp = z;
   }
   __syncwarp();
-  v = (N - 1 - lane >= 0) ? y[N - 1 - lane] : 0.f;
-  for (int i = N - 1; i >= 0; --i) {
-    const int h = (N - 1 - i) & 31, d = (lane - (N - 1 - i)) & 31;
-    const float coef = (d >= 1 && d <= bw && i - d >= 0) ? Ls[i * ls + d] : 0.f;
-    const float refill = (i - 32 >= 0) ? y[i - 32] : 0.f;
-    const float xi = __shfl_sync(full, v, h);
-    v = (lane == h) ? refill : v - coef * xi;
-    y[i] = xi;
+  float xn = 0.f;
+  for (int k = nbk - 1; k >= 0; --k) {
+    float sv = y[k * kTB + lane];
+    if (k + 1 < nbk) {
+      const float* Tn = tiles + (size_t)(k + 1) * kTT + lane;  // column `lane` of tile k + 1
+      float s1 = 0.f;
+#pragma unroll
+      for (int m = 0; m < kTB; m += 2) {
+        const float x0 = __shfl_sync(full, xn, m), x1 = __shfl_sync(full, xn, m + 1);
+        sv -= (lane > m ? Tn[m * kTP] : 0.f) * x0;
+        s1 -= (lane > m + 1 ? Tn[(m + 1) * kTP] : 0.f) * x1;
+      }
+      sv += s1;
+    }
+    const float* Tc = tiles + (size_t)k * kTT + lane;  // column `lane` of tile k
+    float x = sv, x1 = 0.f;
+#pragma unroll
+    for (int m = 0; m < kTB; m += 2) {
+      const float s0 = __shfl_sync(full, sv, m), s1 = __shfl_sync(full, sv, m + 1);
+      x += (m > lane ? Tc[m * kTP] : 0.f) * s0;
+      x1 += (m + 1 > lane ? Tc[(m + 1) * kTP] : 0.f) * s1;
+    }
+    x += x1;
+    y[k * kTB + lane] = x;
+    xn = x;
   }
   __syncwarp();
 }
@@ -414,17 +453,17 @@ __device__ void warp_pencil_apply(const SubEigArgs& a, int b, const double* K, c
   __syncwarp();
 }
 
-// y = A~^{-1} rhs (add: y += A~^{-1} rhs) by one warp, all N rows. A~ is A with the FP32 band
-// factor of K: t = K~^{-1} rhs_band, y_border = S^{-1} (rhs_border - G_a^T t) with the FP64
+// y = A~^{-1} rhs (add: y += A~^{-1} rhs) by one warp, all N rows. A~ is A with the FP32
+// factor of K (blocked form): t = K~^{-1} rhs_band, y_border = S^{-1} (rhs_border - G_a^T t) with the FP64
 // Cholesky factor of the Schur complement S = A_q - G_a^T Z, y_band = t - Z y_border.
-// yb: the warp's nb floats of shared scratch; w2: its nbord doubles.
-__device__ void warp_bordered_solve(const SubEigArgs& a, const float* Lf, int ls, const float* invDf,
+// yb: the warp's 32 nbk floats of shared scratch; w2: its nbord doubles.
+__device__ void warp_bordered_solve(const SubEigArgs& a, const float* tiles, const float* invDf,
                                     const double* Ga, const double* Z, const double* Sq, double* w2, float* yb,
                                     const double* rhs, double* y, bool add) {
-  const int lane = threadIdx.x & 31, nb = a.nb, nbd = a.nbord;
-  for (int r = lane; r < nb; r += 32) yb[r] = (float)rhs[r];
+  const int lane = threadIdx.x & 31, nb = a.nb, nbd = a.nbord, nbk = sub_eig_nbk(nb);
+  for (int r = lane; r < nbk * kTB; r += 32) yb[r] = r < nb ? (float)rhs[r] : 0.f;
   __syncwarp();
-  warp_band_solve(Lf, ls, invDf, yb, nb, a.bwk);
+  warp_block_solve(tiles, invDf, yb, nbk);
   if (nbd) {
     double gt[MLEV_MAX_EIGENPAIRS];
     for (int i = 0; i < nbd; ++i) {
@@ -485,10 +524,14 @@ __global__ void __launch_bounds__(1024) k_sub_eig(DevGeom G, SubEigArgs a) {
   double* Sq = thp + kSMax;           // nbord x nbord Cholesky factor of the Schur complement
   double* y2 = Sq + MLEV_MAX_EIGENPAIRS * MLEV_MAX_EIGENPAIRS;  // per warp: nbord values
   double* wkd = y2 + 32 * MLEV_MAX_EIGENPAIRS;                    // small_eig workspace (4 * 256)
-  float* Lf = reinterpret_cast<float*>(wkd + 4 * kSMax * kSMax);
-  float* invDf = Lf + (size_t)nb * ls;
-  float* ybuf = invDf + nb;           // s columns of nb floats
-  int* pairs = reinterpret_cast<int*>(ybuf + (size_t)s * nb);
+  // FP32 factor: the band (nb rows of ls floats) is factored at the end of the tile region and
+  // converted block by block into the tiles, which never overwrite a band row not yet read
+  const int nbk = sub_eig_nbk(nb), nb32 = nbk * kTB;
+  float* tiles = reinterpret_cast<float*>(wkd + 4 * kSMax * kSMax);
+  float* Lf = tiles + ((size_t)nbk * kTT - (size_t)nb * ls);
+  float* invDf = tiles + (size_t)nbk * kTT;  // nb32 entries, 1 on the padding rows
+  float* ybuf = invDf + nb32;                // s columns of nb32 floats
+  int* pairs = reinterpret_cast<int*>(ybuf + (size_t)s * nb32);
   __shared__ int done, conv, phase2, hi_now, p2it;
   __shared__ double rpart[32], dpart[32], res_final;
   const double* K = a.K + (long long)b * a.kstride;
@@ -520,15 +563,47 @@ __global__ void __launch_bounds__(1024) k_sub_eig(DevGeom G, SubEigArgs a) {
     const int r = e / ls, d = e % ls;
     if (d >= 1 && r - d >= 0) Lf[e] *= invDf[r - d];
   }
+  for (int r = nb + tid; r < nb32; r += blockDim.x) invDf[r] = 1.f;
+  __syncthreads();
+  // ---- blocked form (32 warps x 32 lanes: one thread per tile entry). Tile k is written at
+  // [k kTT, (k + 1) kTT), below the band rows of the blocks after k (the band region starts
+  // nbk kTT - nb ls floats in, and ls <= 32 < kTP), so only block k's own rows can overlap:
+  // they are read before the barrier, the tile written after it
+  for (int k = 0; k < nbk; ++k) {
+    auto Lkk = [&](int i, int j) {  // L(32 k + i, 32 k + j), j < i
+      const int r = k * kTB + i, d = i - j;
+      return (d <= a.bwk && r < nb) ? Lf[(size_t)r * ls + d] : 0.f;
+    };
+    // warp c: column c of T_k = L_kk^{-1} (lane i holds entry i): L_kk x = e_c
+    float x = lane == warp ? 1.f : 0.f;
+    for (int j = warp; j < kTB; ++j) {
+      const float xj = __shfl_sync(0xffffffffu, x, j);
+      if (lane > j) x -= Lkk(lane, j) * xj;
+    }
+    // thread (row warp, column lane): C_k[warp][lane] = L(32 k + warp, 32 (k - 1) + lane)
+    float cpl = 0.f;
+    {
+      const int r = k * kTB + warp, d = kTB + warp - lane;
+      if (k > 0 && lane > warp && d <= a.bwk && r < nb) cpl = Lf[(size_t)r * ls + d];
+    }
+    __syncthreads();
+    float* T = tiles + (size_t)k * kTT;
+    if (lane > warp) {
+      T[lane * kTP + warp] = x;    // T_k[lane][warp], below the diagonal
+      T[warp * kTP + lane] = cpl;  // C_k[warp][lane], above it
+    } else if (lane == warp) {
+      T[lane * kTP + lane] = 0.f;
+    }
+  }
   __syncthreads();
   // ---- border: Z_i = K^{-1} G_a,i (warp i), S = A_q - G_a^T Z, Cholesky (thread 0)
   const int nbd = a.nbord;
   if (nbd) {
     for (int i = warp; i < nbd; i += nwarp) {
-      float* yb = ybuf + (size_t)i * nb;
-      for (int r = lane; r < nb; r += 32) yb[r] = (float)Ga[(long long)i * nb + r];
+      float* yb = ybuf + (size_t)i * nb32;
+      for (int r = lane; r < nb32; r += 32) yb[r] = r < nb ? (float)Ga[(long long)i * nb + r] : 0.f;
       __syncwarp();
-      warp_band_solve(Lf, ls, invDf, yb, nb, a.bwk);
+      warp_block_solve(tiles, invDf, yb, nbk);
       for (int r = lane; r < nb; r += 32) Z[(long long)i * nb + r] = (double)yb[r];
     }
     __syncthreads();
@@ -591,15 +666,15 @@ __global__ void __launch_bounds__(1024) k_sub_eig(DevGeom G, SubEigArgs a) {
       double* y = Y + (long long)warp * N;
       double* t1 = BY + (long long)warp * N;
       double* t2 = AY + (long long)warp * N;
-      float* yb = ybuf + (size_t)warp * nb;
+      float* yb = ybuf + (size_t)warp * nb32;
       double* w2 = y2 + warp * MLEV_MAX_EIGENPAIRS;
       warp_pencil_apply<false, true>(a, b, K, M, Ga, Gb, x, nullptr, t1);
-      warp_bordered_solve(a, Lf, ls, invDf, Ga, Z, Sq, w2, yb, t1, y, false);
+      warp_bordered_solve(a, tiles, invDf, Ga, Z, Sq, w2, yb, t1, y, false);
       for (int k = 0; k < nref; ++k) {
         warp_pencil_apply<true, false>(a, b, K, M, Ga, Gb, y, t2, nullptr);
         for (int r = lane; r < N; r += 32) t2[r] = t1[r] - t2[r];
         __syncwarp();
-        warp_bordered_solve(a, Lf, ls, invDf, Ga, Z, Sq, w2, yb, t2, y, true);
+        warp_bordered_solve(a, tiles, invDf, Ga, Z, Sq, w2, yb, t2, y, true);
       }
       warp_pencil_apply<true, true>(a, b, K, M, Ga, Gb, y, t2, t1);
     }
@@ -804,7 +879,8 @@ void launch_border_prep(const DevGeom& G, int Breal, int q, const double* partia
 size_t sub_eig_smem_bytes(int nb, int bwk, int s) {
   const size_t dbl = (size_t)(3 * kSMax * kSMax + 2 * kSMax + MLEV_MAX_EIGENPAIRS * MLEV_MAX_EIGENPAIRS +
                               32 * MLEV_MAX_EIGENPAIRS + 4 * kSMax * kSMax) * 8;
-  const size_t flt = ((size_t)nb * sub_eig_ls(bwk) + nb + (size_t)s * nb) * 4;
+  const size_t nb32 = (size_t)sub_eig_nbk(nb) * kTB;
+  const size_t flt = ((size_t)sub_eig_nbk(nb) * kTT + nb32 + (size_t)s * nb32) * 4;
   return dbl + flt + (size_t)bwk * (bwk + 1) / 2 * 4 + 64;
 }
 void launch_sub_eig(const DevGeom& G, const SubEigArgs& a, int Breal, cudaStream_t s) {
