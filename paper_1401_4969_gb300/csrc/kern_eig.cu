@@ -1029,6 +1029,10 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
       factored = true;
     }
     __syncthreads();
+    // Newton from the extrapolated shift: it lies within ~1e-7 of lambda_L where alpha / beta
+    // lies ~1e-4 above it, which saves a step (S(sigma) factored, so sigma is below the pole;
+    // from either side of the root the safeguarded iteration converges)
+    if (factored && sig > 0.0 && sig < mu) mu = sig;
   }
   for (; it < a.max_iter; ++it) {
     bool ok = factored && solve(mu, kNewtonTarget);
