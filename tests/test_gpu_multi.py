@@ -109,3 +109,37 @@ def test_one_eigenpair_through_the_several_path_matches_the_single():
     assert abs(float(lam1[0]) - ML.solve(p).lam) <= 1e-8 * ML.solve(p).lam
     s1.close()
     s2.close()
+
+
+def test_six_eigenpairs_full_size_against_stored_oracle():
+    """The 6 smallest eigenpairs of the 1M-unknown unit square (6 levels; the bench's
+    eigenpairs leg) against the oracle's stored eigenvalues (tests/golden/oracle_c2_q6.json,
+    written by tests/golden/make_golden.py): every lambda_i within the 1e-8 mixed bar, and
+    the eigenvectors b-orthonormal."""
+    import json
+    import os
+
+    from paper_1401_4969_gb300 import mlev
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_c2_q6.json")
+    with open(path) as f:
+        gold = json.load(f)
+    p = W.config2()
+    assert gold["problem"] == p.name and gold["q"] == 6
+    s = mlev.Solver(p, eigenpairs=6)
+    lam_t, u_t = s.alloc_outputs(want_u=True)
+    rep = s.solve_into(mlev.default_opts(precision=1), lam_t, u_t, report=True)
+    assert rep["status_flags"] == 0
+    lam = lam_t.cpu().numpy().reshape(6)
+    u = u_t.cpu().numpy().reshape(6, -1)
+    s.close()
+    ref = np.array(gold["lams"])
+    assert np.all(np.abs(lam - ref) <= 1e-8 * ref), (lam, ref)
+    lv = np.array(gold["lam_levels"])
+    assert np.all(np.abs(np.array(rep["lambda_levels"]) - lv[:, 0]) <= 1e-8 * lv[:, 0])
+    # b(u_i, u_j) with the lumped-free consistent mass, via the oracle's level-6 matrix
+    h = ML.build(p)
+    lv6 = h.levels[p.levels]
+    key = lv6.key(lv6.pts)
+    G = np.stack([u[i][key] for i in range(6)], axis=1)
+    assert np.allclose(G.T @ (h.M[p.levels] @ G), np.eye(6), atol=1e-8)
