@@ -5,8 +5,10 @@
 // -- with the grid values held in registers instead of shared memory:
 //
 // * A block of 8 warps covers a 128 x 64 box of one grid; warp w holds rows 8w .. 8w+7 of
-//   the box and lane l holds columns 4l .. 4l+3 of every one of those rows (x and f as
-//   float4 loads straight from the pools), so a half-sweep reads the north / south
+//   the box and lane l holds columns 4l .. 4l+3 of every one of those rows (x and f as float4
+//   loads straight from the pools; f stays in registers for kappa = 1 and goes to shared
+//   memory for kappa per coarse cell, whose coefficient selection needs the registers for a
+//   third block per SM), so a half-sweep reads the north / south
 //   neighbours from the thread's own registers, the west / east neighbour across a lane
 //   boundary by one warp shuffle per row, and the rows across warp boundaries from a small
 //   shared-memory exchange (one barrier per half-sweep).
@@ -126,13 +128,22 @@ __device__ __forceinline__ CoarseK opaque(CoarseK c) {
 }
 
 template <int KK, int C>
-__device__ __forceinline__ void rhalf_sweep(RegTile& x, const RegTile& f, unsigned mask, const float (&below)[4],
+__device__ __forceinline__ void rhalf_sweep(RegTile& x, const RegTile& f, const float4* fw, unsigned mask,
+                                            const float (&below)[4],
                                             const float (&above)[4], const KappaDev& kv, const CoarseK& ck0, int p,
                                             int l, int gi0, int gj0) {
   const CoarseK ck = KK == MLEV_KAPPA_PER_COARSE_CELL ? opaque(ck0) : ck0;
 #pragma unroll
   for (int q = 0; q < kRR; ++q) {
     const int k0 = (C ^ q) & 1;
+    float fq[4];
+    if constexpr (KK == MLEV_KAPPA_PER_COARSE_CELL) {  // f of row q from shared memory
+      const float4 fv = fw[q * 32 + (threadIdx.x & 31)];
+      fq[0] = fv.x; fq[1] = fv.y; fq[2] = fv.z; fq[3] = fv.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) fq[k] = f.v[q][k];
+    }
     // the row updates columns k0 and k0 + 2: column 0 needs the west neighbour from lane - 1,
     // column 3 the east neighbour from lane + 1 (one shuffle either way)
     float nb;
@@ -147,10 +158,10 @@ __device__ __forceinline__ void rhalf_sweep(RegTile& x, const RegTile& f, unsign
       const float xn = q == kRR - 1 ? above[k] : x.v[q == kRR - 1 ? kRR - 1 : q + 1][k];
       float nv;  // plain Gauss-Seidel (omega = 1): the node takes the value that zeroes its residual
       if (KK == MLEV_KAPPA_ONE) {
-        nv = ((f.v[q][k] + xe) + (xw + xn) + xs) * 0.25f;
+        nv = ((fq[k] + xe) + (xw + xn) + xs) * 0.25f;
       } else {
         const EW<float> w = rweights<KK>(kv, ck, p, l, gi0, gj0, q, k);
-        nv = div_diag<float>((f.v[q][k] + w.e * xe) + (w.w * xw + w.n * xn) + w.s * xs, (w.e + w.w) + (w.n + w.s));
+        nv = div_diag<float>((fq[k] + w.e * xe) + (w.w * xw + w.n * xn) + w.s * xs, (w.e + w.w) + (w.n + w.s));
       }
       if (mask & (1u << (q * 4 + k))) x.v[q][k] = nv;
     }
@@ -167,6 +178,21 @@ __device__ __forceinline__ void rload(RegTile& t, const float* base, int pitch, 
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (colok && j >= 0 && j <= ny) v = __ldg(reinterpret_cast<const float4*>(base + (long long)j * pitch + c0));
     t.v[q][0] = v.x; t.v[q][1] = v.y; t.v[q][2] = v.z; t.v[q][3] = v.w;
+  }
+}
+
+// Loads f rows [r0, r0 + 8) x columns [c0, c0 + 4) into the block's shared rows 8 w .. 8 w + 7
+// (float4 per lane, zeros outside as rload): f is read once per half-sweep and row, so it
+// lives in shared memory and its 32 values leave the thread's registers.
+__device__ __forceinline__ void rload_sm(float4* fs, const float* base, int pitch, int ny, int c0, int r0, int w,
+                                         int lane) {
+  const bool colok = c0 >= 0 && c0 + 3 < pitch;
+#pragma unroll
+  for (int q = 0; q < kRR; ++q) {
+    const int j = r0 + q;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (colok && j >= 0 && j <= ny) v = __ldg(reinterpret_cast<const float4*>(base + (long long)j * pitch + c0));
+    fs[(w * kRR + q) * 32 + lane] = v;
   }
 }
 
@@ -224,10 +250,15 @@ __device__ __forceinline__ RGrid rgrid(const GridDesc& g) {
 // Down leg on one tile: NU red-black sweeps (red first), the residual, and its restriction
 // to the next coarser grid (f_c = P^T r, x_c = 0) for the coarse nodes of the tile.
 template <int KK, int NU, bool FULL>
-__global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restrict__ tiles,
+__global__ void __launch_bounds__(256, KK == MLEV_KAPPA_ONE ? 2 : 3) k_rdown(DevGeom G, const Tile* __restrict__ tiles,
                                                   const float* __restrict__ X, float* XC, float* __restrict__ XS,
                                                   float* F, int black_zero) {
+  // kappa = 1: f in registers (2 blocks per SM); kappa per coarse cell: f, then the residual,
+  // in shared memory (3 blocks per SM: the coefficient selection needs registers). Each was the
+  // faster form on its workload.
+  constexpr bool SMF = KK == MLEV_KAPPA_PER_COARSE_CELL;
   __shared__ float4 xbuf[2][2][kRWarps][32];
+  extern __shared__ float4 fs[];  // SMF: [64 rows][32 lanes]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const Tile t = tiles[blockIdx.x];
   const GridDesc& gd = G.grids[t.grid];
@@ -235,9 +266,11 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
   const GridDesc& gcd = G.grids[t.grid + 1];
   const RGrid gc = rgrid(gcd);
   const int c0 = t.x0 - kRHX + 4 * lane, r0 = t.y0 - kRHY + kRR * w;
+  float4* fw = fs + w * kRR * 32;  // this warp's shared rows (each thread reads only its own entries)
   RegTile x, f;
   rload(x, X + g.off, g.pitch, g.ny, c0, r0);
-  rload(f, F + g.off, g.pitch, g.ny, c0, r0);
+  if constexpr (SMF) rload_sm(fs, F + g.off, g.pitch, g.ny, c0, r0, w, lane);
+  else rload(f, F + g.off, g.pitch, g.ny, c0, r0);
   const unsigned mask = rmask<FULL>(G, gd, c0, r0);
 #pragma unroll
   for (int q = 0; q < kRR; ++q)
@@ -250,19 +283,27 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
 #pragma unroll
   for (int s = 0; s < NU; ++s) {
     exchange_rows(xbuf[0], x, below, above, w, lane);
-    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
+    rhalf_sweep<KK, 0>(x, f, fw, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
     exchange_rows(xbuf[1], x, below, above, w, lane);
-    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
+    rhalf_sweep<KK, 1>(x, f, fw, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
   }
   rstore(x, XS + g.off, g.pitch, g.ny, c0, r0, t.y0, lane);
-  // residual r = f - A x in f's registers (0 off the unknowns); with black_zero only the red
-  // nodes (the black residuals vanish after the closing black half-sweep)
+  // residual r = f - A x (0 off the unknowns), into f's registers or shared entries; with
+  // black_zero only the red nodes (the black residuals vanish after the closing black half-sweep)
   exchange_rows(xbuf[0], x, below, above, w, lane);
   const CoarseK ckr = KK == MLEV_KAPPA_PER_COARSE_CELL ? opaque(ck) : ck;
 #pragma unroll
   for (int q = 0; q < kRR; ++q) {
     const float wx = __shfl_up_sync(0xffffffffu, x.v[q][3], 1);
     const float ex = __shfl_down_sync(0xffffffffu, x.v[q][0], 1);
+    float fq[4];
+    if constexpr (SMF) {
+      const float4 fv = fw[q * 32 + lane];
+      fq[0] = fv.x; fq[1] = fv.y; fq[2] = fv.z; fq[3] = fv.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) fq[k] = f.v[q][k];
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const float xw = k == 0 ? wx : x.v[q][k == 0 ? 0 : k - 1];
@@ -270,48 +311,76 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
       const float xs = q == 0 ? below[k] : x.v[q == 0 ? 0 : q - 1][k];
       const float xn = q == kRR - 1 ? above[k] : x.v[q == kRR - 1 ? kRR - 1 : q + 1][k];
       if (black_zero && ((q + k) & 1)) {  // black: zero after the closing black half-sweep
-        f.v[q][k] = 0.f;
+        fq[k] = 0.f;
         continue;
       }
       float r;
       if (KK == MLEV_KAPPA_ONE) {
-        r = f.v[q][k] - (4.0f * x.v[q][k] - ((xe + xw) + (xn + xs)));
+        r = fq[k] - (4.0f * x.v[q][k] - ((xe + xw) + (xn + xs)));
       } else {
         const EW<float> wt = rweights<KK>(G.kap, ckr, g.problem, g.level, gi0, gj0, q, k);
-        r = f.v[q][k] - (((wt.e + wt.w) + (wt.n + wt.s)) * x.v[q][k] - ((wt.e * xe + wt.w * xw) + (wt.n * xn + wt.s * xs)));
+        r = fq[k] - (((wt.e + wt.w) + (wt.n + wt.s)) * x.v[q][k] - ((wt.e * xe + wt.w * xw) + (wt.n * xn + wt.s * xs)));
       }
-      f.v[q][k] = (mask & (1u << (q * 4 + k))) ? r : 0.f;
+      fq[k] = (mask & (1u << (q * 4 + k))) ? r : 0.f;
+    }
+    if constexpr (SMF) {
+      fw[q * 32 + lane] = make_float4(fq[0], fq[1], fq[2], fq[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f.v[q][k] = fq[k];
     }
   }
-  // restriction: coarse node (I, J) = fine (2I, 2J) = register (q, k), q even, k in {0, 2};
-  // needs r of the row below the warp (its q = -1) and of the column left of the lane
-  exchange_rows(xbuf[1], f, below, above, w, lane);
+  // restriction: coarse node (I, J) = fine (2I, 2J) = register (q, k), q even, k in {0, 2}
   const bool out_col = lane >= 2 && lane < 30;
+  float val[kRR / 2][2];
+  if constexpr (SMF) {
+    // from the residuals of the shared box ([64][128] floats; its outer ring reads 0, and no
+    // output depends on it)
+    __syncthreads();
+    const float* rs = reinterpret_cast<const float*>(fs);
+    auto res = [&](int R, int Cc) { return (R >= 0 && Cc >= 0) ? rs[R * kRW + Cc] : 0.f; };
+#pragma unroll
+    for (int q = 0; q < kRR; q += 2) {
+      const int R = w * kRR + q;
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const int Cc = 4 * lane + 2 * kk;
+        float half = res(R + 1, Cc + 1) + res(R - 1, Cc - 1);
+        if (!black_zero) half += res(R, Cc + 1) + res(R, Cc - 1) + res(R + 1, Cc) + res(R - 1, Cc);
+        val[q / 2][kk] = res(R, Cc) + 0.5f * half;
+      }
+    }
+  } else {
+    // needs r of the row below the warp (its q = -1) and of the column left of the lane
+    exchange_rows(xbuf[1], f, below, above, w, lane);
+#pragma unroll
+    for (int q = 0; q < kRR; q += 2) {
+      const float wr0 = __shfl_up_sync(0xffffffffu, f.v[q][3], 1);  // r(q, -1)
+      const float wrm = __shfl_up_sync(0xffffffffu, q == 0 ? below[3] : f.v[q == 0 ? 0 : q - 1][3], 1);  // r(q-1, -1)
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * kk;
+        const float rc = f.v[q][k];
+        const float rne = f.v[q + 1][k + 1];
+        const float rsw = k == 0 ? wrm : (q == 0 ? below[k - 1 < 0 ? 0 : k - 1] : f.v[q == 0 ? 0 : q - 1][k - 1 < 0 ? 0 : k - 1]);
+        float half = rne + rsw;
+        if (!black_zero) {
+          const float re = f.v[q][k + 1];
+          const float rw = k == 0 ? wr0 : f.v[q][k - 1 < 0 ? 0 : k - 1];
+          const float rn = f.v[q + 1][k];
+          const float rs = q == 0 ? below[k] : f.v[q == 0 ? 0 : q - 1][k];
+          half += re + rw + rn + rs;
+        }
+        val[q / 2][kk] = rc + 0.5f * half;
+      }
+    }
+  }
 #pragma unroll
   for (int q = 0; q < kRR; q += 2) {
-    const float wr0 = __shfl_up_sync(0xffffffffu, f.v[q][3], 1);  // r(q, -1)
-    const float wrm = __shfl_up_sync(0xffffffffu, q == 0 ? below[3] : f.v[q == 0 ? 0 : q - 1][3], 1);  // r(q-1, -1)
     const int j = r0 + q;
     if (!out_col || j < t.y0 || j >= t.y0 + kROH) continue;
     const int J = j >> 1;
     if (J > gc.ny) continue;
-    float val[2];
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      const int k = 2 * kk;
-      const float rc = f.v[q][k];
-      const float rne = f.v[q + 1][k + 1];
-      const float rsw = k == 0 ? wrm : (q == 0 ? below[k - 1 < 0 ? 0 : k - 1] : f.v[q == 0 ? 0 : q - 1][k - 1 < 0 ? 0 : k - 1]);
-      float half = rne + rsw;
-      if (!black_zero) {
-        const float re = f.v[q][k + 1];
-        const float rw = k == 0 ? wr0 : f.v[q][k - 1 < 0 ? 0 : k - 1];
-        const float rn = f.v[q + 1][k];
-        const float rs = q == 0 ? below[k] : f.v[q == 0 ? 0 : q - 1][k];
-        half += re + rw + rn + rs;
-      }
-      val[kk] = rc + 0.5f * half;
-    }
     const int I = c0 >> 1;
     float* fr = F + gc.off + (long long)J * gc.pitch;
     float* xr = XC + gc.off + (long long)J * gc.pitch;
@@ -320,7 +389,7 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
       const int Ik = I + kk;
       if (Ik > gc.nx) continue;
       const bool u = FULL ? (Ik >= 1 && J >= 1 && Ik < gc.nx && J < gc.ny) : is_unknown(G, gcd, Ik, J);
-      fr[Ik] = u ? val[kk] : 0.f;
+      fr[Ik] = u ? val[q / 2][kk] : 0.f;
       xr[Ik] = 0.f;
     }
   }
@@ -330,11 +399,12 @@ __global__ void __launch_bounds__(256, 2) k_rdown(DevGeom G, const Tile* __restr
 // red_only only the red nodes, since a plain Gauss-Seidel black half-sweep opens the
 // post-smoothing), then NU red-black sweeps (black first). Reads x from XS, writes X.
 template <int KK, int NU, bool FULL>
-__global__ void __launch_bounds__(256, 2) k_rup(DevGeom G, const Tile* __restrict__ tiles,
+__global__ void __launch_bounds__(256, KK == MLEV_KAPPA_ONE ? 2 : 3) k_rup(DevGeom G, const Tile* __restrict__ tiles,
                                                 const float* __restrict__ XS, float* X, const float* __restrict__ F,
                                                 int red_only) {
   __shared__ float4 xbuf[2][2][kRWarps][32];
   __shared__ float xc[34][66];  // coarse nodes [by0/2, by0/2 + 33] x [bx0/2, bx0/2 + 65]
+  extern __shared__ float4 fs[];  // kappa per coarse cell: [64 rows][32 lanes], the box's f
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const Tile t = tiles[blockIdx.x];
   const GridDesc& gd = G.grids[t.grid];
@@ -353,9 +423,11 @@ __global__ void __launch_bounds__(256, 2) k_rup(DevGeom G, const Tile* __restric
       xc[jj][ii] = v;
     }
   }
-  RegTile x, f;
+  RegTile x, f;  // f in registers for kappa = 1, in shared memory for kappa per coarse cell
   rload(x, XS + g.off, g.pitch, g.ny, c0, r0);
-  rload(f, F + g.off, g.pitch, g.ny, c0, r0);
+  if constexpr (KK == MLEV_KAPPA_PER_COARSE_CELL) rload_sm(fs, F + g.off, g.pitch, g.ny, c0, r0, w, lane);
+  else rload(f, F + g.off, g.pitch, g.ny, c0, r0);
+  const float4* fw = fs + w * kRR * 32;
   const unsigned mask = rmask<FULL>(G, gd, c0, r0);
   __syncthreads();
   // prolongation (exact P1 interpolation on the SW-NE mesh)
@@ -383,9 +455,9 @@ __global__ void __launch_bounds__(256, 2) k_rup(DevGeom G, const Tile* __restric
 #pragma unroll
   for (int s = 0; s < NU; ++s) {  // two exchange buffers in turn: one barrier per half-sweep
     exchange_rows(xbuf[0], x, below, above, w, lane);
-    rhalf_sweep<KK, 1>(x, f, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
+    rhalf_sweep<KK, 1>(x, f, fw, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
     exchange_rows(xbuf[1], x, below, above, w, lane);
-    rhalf_sweep<KK, 0>(x, f, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
+    rhalf_sweep<KK, 0>(x, f, fw, mask, below, above, G.kap, ck, g.problem, g.level, gi0, gj0);
   }
   rstore(x, X + g.off, g.pitch, g.ny, c0, r0, t.y0, lane);
 }
@@ -396,21 +468,43 @@ bool rkernels_support(int kappa_kind, int level, int pre, int post, double omega
          pre <= 2 && post >= 1 && post <= 2 && omega == 1.0;
 }
 
+// dynamic shared memory of both legs: the box's f, 64 rows of 32 float4
+constexpr int kRFsBytes = kRR * kRWarps * 32 * (int)sizeof(float4);
+
+// the up leg's static buffers plus f pass the 48 KB default: raise the limit once per kernel
+template <typename Kern>
+static void allow_fs(Kern k, bool& done) {
+  if (!done) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kRFsBytes);
+    done = true;
+  }
+}
+
 template <int KK, int NU>
 static void rdown_kk(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F,
                      int black_zero, cudaStream_t s) {
-  if (full)
-    k_rdown<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, X, X, XS, F, black_zero);
-  else
-    k_rdown<KK, NU, false><<<n, 256, 0, s>>>(G, tiles, X, X, XS, F, black_zero);
+  constexpr int fsb = KK == MLEV_KAPPA_PER_COARSE_CELL ? kRFsBytes : 0;
+  static bool a0 = false, a1 = false;
+  if (full) {
+    if (fsb) allow_fs(k_rdown<KK, NU, true>, a1);
+    k_rdown<KK, NU, true><<<n, 256, fsb, s>>>(G, tiles, X, X, XS, F, black_zero);
+  } else {
+    if (fsb) allow_fs(k_rdown<KK, NU, false>, a0);
+    k_rdown<KK, NU, false><<<n, 256, fsb, s>>>(G, tiles, X, X, XS, F, black_zero);
+  }
 }
 template <int KK, int NU>
 static void rup_kk(const DevGeom& G, const Tile* tiles, int n, int full, const float* XS, float* X, const float* F,
                    int red_only, cudaStream_t s) {
-  if (full)
-    k_rup<KK, NU, true><<<n, 256, 0, s>>>(G, tiles, XS, X, F, red_only);
-  else
-    k_rup<KK, NU, false><<<n, 256, 0, s>>>(G, tiles, XS, X, F, red_only);
+  constexpr int fsb = KK == MLEV_KAPPA_PER_COARSE_CELL ? kRFsBytes : 0;
+  static bool a0 = false, a1 = false;
+  if (full) {
+    if (fsb) allow_fs(k_rup<KK, NU, true>, a1);
+    k_rup<KK, NU, true><<<n, 256, fsb, s>>>(G, tiles, XS, X, F, red_only);
+  } else {
+    if (fsb) allow_fs(k_rup<KK, NU, false>, a0);
+    k_rup<KK, NU, false><<<n, 256, fsb, s>>>(G, tiles, XS, X, F, red_only);
+  }
 }
 
 void launch_rdown(const DevGeom& G, const Tile* tiles, int n, int full, float* X, float* XS, float* F, int nu,
