@@ -194,7 +194,7 @@ __device__ void warp_block_solve(const float* tiles, const float* invD, float* y
 }
 
 constexpr int kSMax = 16;  // largest block of the subspace iteration
-constexpr int kCheck = 4;  // FP64 Rayleigh-Ritz and residual test every kCheck-th step of the FP64 phase
+constexpr int kCheck = 4;  // Rayleigh-Ritz (FP64 and the residual test in the FP64 phase) every kCheck-th step
 
 // row stride of the FP32 band factor: bw + 1 rounded up to even (conflict-free coefficient loads)
 __host__ __device__ inline int sub_eig_ls(int bwk) { return (bwk + 2) & ~1; }
@@ -404,6 +404,40 @@ __global__ void k_border_prep(DevGeom G, int q, const double* partials, const do
   }
 }
 
+// W = L^{-T} for B = L L^T (FP32, warp 0; W row-major s x s, W[k * s + c]): X = Y W has
+// B-orthonormal columns to FP32 accuracy. Used between the Rayleigh-Ritz steps, where the
+// block only has to stay well conditioned (span(X) = span(Y)). wk: 2 * 16 * 16 floats.
+__device__ void chol_orth_warp(int s, const double* B, double* W, float* wk) {
+  const int lane = threadIdx.x & 31;
+  float* L = wk;
+  float* Wt = wk + kSMax * kSMax;
+  for (int j = 0; j < s; ++j) {
+    if (lane == 0) {
+      float d = (float)B[j * s + j];
+      for (int k = 0; k < j; ++k) d -= L[j * kSMax + k] * L[j * kSMax + k];
+      L[j * kSMax + j] = sqrtf(d > 0.f ? d : 1e-30f);
+    }
+    __syncwarp();
+    if (lane > j && lane < s) {
+      float v = (float)B[lane * s + j];
+      for (int k = 0; k < j; ++k) v -= L[lane * kSMax + k] * L[j * kSMax + k];
+      L[lane * kSMax + j] = v / L[j * kSMax + j];
+    }
+    __syncwarp();
+  }
+  if (lane < s) {  // column `lane` of L^{-T}: L^T w = e_lane, from the last row up
+    for (int i = s - 1; i >= 0; --i) {
+      float v = i == lane ? 1.f : 0.f;
+      for (int k = i + 1; k < s; ++k) v -= L[k * kSMax + i] * Wt[k * kSMax + lane];
+      Wt[i * kSMax + lane] = v / L[i * kSMax + i];
+    }
+  }
+  __syncwarp();
+  if (lane < s)
+    for (int i = 0; i < s; ++i) W[i * s + lane] = (double)Wt[i * kSMax + lane];
+  __syncwarp();
+}
+
 // A v and / or B v of the (bordered) pencil, all N = nb + nbord rows, by one warp (every lane
 // calls it: the border rows are warp sums). Band rows: the band has nonzeros only on the
 // diagonals 0, 1, nx - 1, nx (b = nx - 1 unknowns per grid row), plus the border columns.
@@ -502,11 +536,13 @@ __device__ void warp_bordered_solve(const SubEigArgs& a, const float* tiles, con
 // step 3 on V_{0H} + span{u~_1..u~_q}). A^{-1} uses the FP32 band LDL^T of K in shared memory
 // (warp-parallel solves, one column per warp) and, with a border, the q x q Schur complement
 // S = A_q - G_a^T K^{-1} G_a; the products A Y, B Y, the Gram matrices and the Ritz values are
-// FP64. Columns of X live in global memory. Two phases:
-// * while the q wanted Ritz values change by more than tol (relative): one FP32-factor solve
-//   per column and FP32 Jacobi on the small pencil;
-// * then two steps of iterative refinement against the FP64 pencil per solve, and every
-//   kCheck-th step FP64 Jacobi and the residual test: stop when every wanted Ritz pair has
+// FP64. Columns of X live in global memory. The Rayleigh-Ritz step on the block runs every
+// kCheck-th step; the steps between only B-orthonormalise it (Cholesky of Y^T B Y in FP32:
+// the iteration's subspace is span(Y) either way). Two phases:
+// * while the q wanted Ritz values change by more than tol (relative) between Rayleigh-Ritz
+//   steps: one FP32-factor solve per column and FP32 Jacobi on the small pencil;
+// * then two steps of iterative refinement against the FP64 pencil per solve, and at each
+//   Rayleigh-Ritz step FP64 Jacobi and the residual test: stop when every wanted Ritz pair has
 //   ||A x - theta B x||_2 <= rtol ||theta B x||_2. A stop on the Ritz values alone would leave
 //   the vectors accurate only to about the square root of tol, and the correction steps carry
 //   the level-1 vectors' error into lambda_{h_n}.
@@ -661,6 +697,10 @@ __global__ void __launch_bounds__(1024) k_sub_eig(DevGeom G, SubEigArgs a) {
     // 32 x 32 level-1 grid, each step multiplies the solve error by it); BY and AY of the
     // column serve as scratch; then A Y and B Y in FP64
     const int nref = phase2 ? 2 : 0;
+    // Rayleigh-Ritz (and A Y) only every kCheck-th step of either phase and at the cap; the
+    // steps between only B-orthonormalise the block
+    const bool rr_it = (phase2 ? (it - p2it) % kCheck == kCheck - 1 : it % kCheck == kCheck - 1) ||
+                       it + 1 == a.max_iter;
     if (warp < s) {
       const double* x = X + (long long)warp * N;
       double* y = Y + (long long)warp * N;
@@ -676,7 +716,8 @@ __global__ void __launch_bounds__(1024) k_sub_eig(DevGeom G, SubEigArgs a) {
         __syncwarp();
         warp_bordered_solve(a, tiles, invDf, Ga, Z, Sq, w2, yb, t2, y, true);
       }
-      warp_pencil_apply<true, true>(a, b, K, M, Ga, Gb, y, t2, t1);
+      if (rr_it) warp_pencil_apply<true, true>(a, b, K, M, Ga, Gb, y, t2, t1);
+      else warp_pencil_apply<false, true>(a, b, K, M, Ga, Gb, y, nullptr, t1);
     }
     __syncthreads();
     // Gram matrices Y^T A Y, Y^T B Y (FP64), entry pairs by warps
@@ -687,9 +728,13 @@ __global__ void __launch_bounds__(1024) k_sub_eig(DevGeom G, SubEigArgs a) {
       const double* ayj = AY + (long long)j * N;
       const double* byj = BY + (long long)j * N;
       double va = 0.0, vb = 0.0;
-      for (int r = lane; r < N; r += 32) {
-        va += yi[r] * ayj[r];
-        vb += yi[r] * byj[r];
+      if (rr_it) {
+        for (int r = lane; r < N; r += 32) {
+          va += yi[r] * ayj[r];
+          vb += yi[r] * byj[r];
+        }
+      } else {
+        for (int r = lane; r < N; r += 32) vb += yi[r] * byj[r];
       }
       for (int o = 16; o > 0; o >>= 1) {
         va += __shfl_down_sync(0xffffffffu, va, o);
@@ -701,11 +746,14 @@ __global__ void __launch_bounds__(1024) k_sub_eig(DevGeom G, SubEigArgs a) {
       }
     }
     __syncthreads();
-    // Rayleigh-Ritz on the block by FP32 Jacobi (it only steers the iteration: X = Y W spans
-    // span(Y) for any invertible W); in the FP64 phase every kCheck-th step by FP64 Jacobi,
+    // between Rayleigh-Ritz steps: B-orthonormalise the block; at them, FP32 Jacobi (it only
+    // steers: X = Y W spans span(Y) for any invertible W) or, in the FP64 phase, FP64 Jacobi,
     // whose Ritz pairs the residual test then checks (FP64 arithmetic runs at a small fraction
-    // of the FP32 rate, and a Jacobi solve costs about as much as a step's band solves)
-    if (warp == 0) {
+    // of the FP32 rate: a Jacobi call costs more than a step's solves)
+    if (warp == 0 && !rr_it) {
+      chol_orth_warp(s, Bh, Wm, reinterpret_cast<float*>(wkd));
+      if (lane == 0) hi_now = 0;
+    } else if (warp == 0) {
       const bool hi = (phase2 && (it - p2it) % kCheck == kCheck - 1) || it + 1 == a.max_iter;
       if (hi) small_eig_warp<double>(s, Ah, Bh, Wm, th, wkd);
       else small_eig_warp<float>(s, Ah, Bh, Wm, th, reinterpret_cast<float*>(wkd));
