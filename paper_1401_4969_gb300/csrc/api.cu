@@ -624,7 +624,7 @@ struct Launcher {
       // (per block: the factor's dynamic memory, the kernel's 22.6 KB of static staging and the
       // 1 KB the runtime reserves)
       const long long aug_slots = (long long)ctx->sm_count * (long long)(ctx->smem_per_sm / (pre_smem + 24 * 1024));
-      rr.use_pre = rr.blocked && rr.smem && L >= 4 && P.bw - 1 <= 16 && P.w_rrpre.bytes > 0 &&
+      rr.use_pre = rr.blocked && rr.smem && L >= 3 && P.bw - 1 <= 16 && P.w_rrpre.bytes > 0 &&
                            pre_smem <= (size_t)kRRSmemMax && aug_blocks <= aug_slots ? 1 : 0;
       const RRPrefactor pf{KH, MH, P.nhb, P.bw, rr.pre, rr.pre_stride};
       go(F_INTERP, 10.0 * nfree, [&] { launch_interp(G, P.glay, a, s); });

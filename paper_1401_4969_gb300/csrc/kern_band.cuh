@@ -164,6 +164,19 @@ __device__ __forceinline__ double coarse_band_mv(const double* A, int bw, int b,
 // Diagonal slot k = 0..3 of the nonzero diagonals d = 0, 1, b, b + 1 of the T_H pencil band.
 __device__ __forceinline__ int coarse_band_diag(int k, int b) { return k < 2 ? k : b + (k - 2); }
 
+// Asynchronous global -> shared copies (no registers held while in flight): 16 bytes (both
+// addresses 16-byte aligned, cached in L2 only) or 8 bytes (8-byte aligned); wait_all
+// returns once every copy this thread issued has landed (a barrier then publishes them).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Block LDL^T of the T_H pencil S = K_H - mu M_H by grid rows (FP32), for unknowns ordered
 // r = (Y-1) b + (X-1): S is block tridiagonal with b x b diagonal blocks S_II (couplings
 // W/E) and sub-diagonal blocks S_{I,I-1} holding only the S and SW couplings (row r: columns
@@ -321,9 +334,92 @@ __device__ __forceinline__ float blk_dot(const float* row, const float* v) {
   return (s0 + s1) + (s2 + s3);
 }
 
+// Half of a 16-wide tile row times a vector held one entry per lane (lane k and k + 16 hold
+// entry k): lanes 0-15 take columns 0-7, lanes 16-31 columns 8-15 (row part a0, a1), the
+// entries come by shuffles; the caller adds the two halves.
+__device__ __forceinline__ float blk_hdot16(const float4 a0, const float4 a1, float v, int k0) {
+  float s0 = a0.x * __shfl_sync(0xffffffffu, v, k0 + 0);
+  float s1 = a0.y * __shfl_sync(0xffffffffu, v, k0 + 1);
+  s0 = fmaf(a0.z, __shfl_sync(0xffffffffu, v, k0 + 2), s0);
+  s1 = fmaf(a0.w, __shfl_sync(0xffffffffu, v, k0 + 3), s1);
+  s0 = fmaf(a1.x, __shfl_sync(0xffffffffu, v, k0 + 4), s0);
+  s1 = fmaf(a1.y, __shfl_sync(0xffffffffu, v, k0 + 5), s1);
+  s0 = fmaf(a1.z, __shfl_sync(0xffffffffu, v, k0 + 6), s0);
+  s1 = fmaf(a1.w, __shfl_sync(0xffffffffu, v, k0 + 7), s1);
+  return s0 + s1;
+}
+
 template <int BS>
 __device__ inline void block_solve_f(const float* Pinv, const float* W, const float* WT, float* yp, float* xp, int b,
                                      int nb) {
+  if constexpr (BS == 16) {
+    // 16-wide rows: the recurrence's vector stays in registers (lane r and r + 16 hold row r)
+    // and moves by shuffles; each half-warp forms half of every row product, and the tile
+    // rows of the next block are loaded one step ahead, so a step's critical path is the
+    // shuffles, 4 FMAs and one exchange of the halves. Padding rows of every tile are zero,
+    // so rows r >= b carry zeros without a test.
+    if (threadIdx.x < 32) {
+      constexpr int LD = blk_ld<16>(), TS = blk_tile<16>();
+      const int lane = threadIdx.x, r = lane & 15, k0 = (lane >> 4) * 8;
+      const bool wr = lane < 16 && r < b;
+      auto row2 = [&](const float* tile, float4& a0, float4& a1) {
+        const float4* p4 = reinterpret_cast<const float4*>(tile + r * LD + k0);
+        a0 = p4[0];
+        a1 = p4[1];
+      };
+      // forward: u_I = y_I - W_I u_{I-1}, u_I back into yp for the backward sweep
+      float u = yp[r];
+      float4 a0, a1;
+      float yn = 0.f;
+      if (nb > 1) {
+        row2(W + TS, a0, a1);
+        yn = yp[BS + r];
+      }
+      for (int I = 1; I < nb; ++I) {
+        const float4 c0 = a0, c1 = a1;
+        const float yc = yn;
+        if (I + 1 < nb) {
+          row2(W + (long long)(I + 1) * TS, a0, a1);
+          yn = yp[(I + 1) * BS + r];
+        }
+        float s = blk_hdot16(c0, c1, u, k0);
+        s += __shfl_xor_sync(0xffffffffu, s, 16);
+        u = yc - s;
+        if (wr) yp[I * BS + r] = u;
+      }
+      __syncwarp();
+      // backward: x_I = P_I^{-1} u_I - W_{I+1}^T x_{I+1}; the P_I^{-1} u_I half products are
+      // off the recurrence and formed one step ahead
+      auto pu_half = [&](int I) {
+        float4 p0, p1;
+        row2(Pinv + (long long)I * TS, p0, p1);
+        const float4* v4 = reinterpret_cast<const float4*>(yp + I * BS + k0);
+        const float4 v0 = v4[0], v1 = v4[1];
+        float s0 = p0.x * v0.x, s1 = p0.y * v0.y;
+        s0 = fmaf(p0.z, v0.z, s0);
+        s1 = fmaf(p0.w, v0.w, s1);
+        s0 = fmaf(p1.x, v1.x, s0);
+        s1 = fmaf(p1.y, v1.y, s1);
+        s0 = fmaf(p1.z, v1.z, s0);
+        s1 = fmaf(p1.w, v1.w, s1);
+        return s0 + s1;
+      };
+      float x = 0.f;
+      float pn = pu_half(nb - 1);
+      for (int I = nb - 1; I >= 0; --I) {
+        float s = pn;
+        float4 t0, t1;
+        if (I + 1 < nb) row2(WT + (long long)(I + 1) * TS, t0, t1);
+        if (I > 0) pn = pu_half(I - 1);
+        if (I + 1 < nb) s -= blk_hdot16(t0, t1, x, k0);
+        s += __shfl_xor_sync(0xffffffffu, s, 16);
+        x = s;
+        if (wr) xp[I * BS + r] = x;
+      }
+    }
+    __syncthreads();
+    return;
+  }
   if (threadIdx.x < 32) {
     constexpr int LD = blk_ld<BS>(), TS = blk_tile<BS>();
     const int r = threadIdx.x;
@@ -349,7 +445,10 @@ __device__ inline void block_solve_f(const float* Pinv, const float* W, const fl
 // eigenvalues of the earlier levels: with d1 = lambda_{L-2} - lambda_{L-1} and
 // d2 = lambda_{L-3} - lambda_{L-2} the differences shrink by r = d2 / d1 per level, so
 // lambda_L ~ lambda_{L-1} - d1 / r. Only a regular sequence (2 <= r <= 8, as for the O(h^2)
-// and corner-limited rates) is used; the Rayleigh-Ritz kernel refines against these
+// and corner-limited rates) is used. Level 3 has only d1 and takes r = 4, the O(h^2) rate of
+// a smooth eigenfunction (on a re-entrant corner the rate is lower and sigma lands a little
+// above lambda_3, which slows the refinement but keeps S(sigma) positive definite while
+// sigma stays below the coarse eigenvalue). The Rayleigh-Ritz kernel refines against these
 // factors and refactors at its own mu if the refinement stalls. `out` holds the layout of
 // mlev_rr_prefactor_stride; `sm` is dynamic shared memory of rr_prefactor_smem bytes.
 // Called by all threads of the block. Only for 16-wide row blocks (b <= 16): the 32-wide
@@ -359,12 +458,18 @@ __device__ inline void rr_prefactor_block(const double* KH, const double* MH, co
   constexpr int BS = 16, TS = BS * (BS + 4);
   const int N = nhb, bw1 = bw + 1, bsz = bw - 1, nbk = N / bsz;
   double sigma = NAN;
-  bool use = L >= 4 && bsz <= BS;
+  bool use = L >= 3 && bsz <= BS;
   if (use) {
-    const double l1 = lamp[L - 1], l2 = lamp[L - 2], l3 = lamp[L - 3];
-    const double d1 = l2 - l1, d2 = l3 - l2;
-    const double r = d2 / d1;
-    use = d1 > 0.0 && d2 > 0.0 && r >= 2.0 && r <= 8.0;
+    const double l1 = lamp[L - 1], l2 = lamp[L - 2];
+    const double d1 = l2 - l1;
+    double r = 4.0;
+    bool regular = true;
+    if (L >= 4) {
+      const double d2 = lamp[L - 3] - l2;
+      r = d2 / d1;
+      regular = d2 > 0.0 && r >= 2.0 && r <= 8.0;
+    }
+    use = d1 > 0.0 && regular;
     sigma = l1 - d1 / r;
   }
   if (!use) {

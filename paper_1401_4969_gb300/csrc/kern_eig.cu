@@ -386,13 +386,14 @@ template void launch_level1<double>(const DevGeom&, const GlobalLayout&, const L
 // suboptimal. Layout: FP32 Gram partials [11][threads], 4 FP64 vectors, 6 FP32 vectors,
 // then x (T) and f (T) of every level and the unknown masks.
 template <typename T, int KK>
-__global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, Level1Args a) {
+__global__ void __launch_bounds__(512, 1) k_level1_sm(DevGeom G, GlobalLayout gl, Level1Args a) {
   extern __shared__ __align__(16) unsigned char l1_raw[];
   __shared__ SmGrid<T> lv[kTailMaxLev];
   __shared__ double red[4];
   __shared__ float gram[12];
   __shared__ float sh_coef[4];
-  __shared__ int sh_flag;
+  __shared__ double sh_rho[2];  // FP64 scalars formed by thread 0, read after the next barrier
+  __shared__ int sh_flag, sh_stop;
   const int p = blockIdx.x, g0 = a.grid_begin + p * a.nlev, nlev = a.nlev;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
   const GridDesc& g = G.grids[g0];
@@ -477,7 +478,12 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
         v[1] += X[q] * MX[q];
       }
       block_sum_t<2>(v, stage, red);
-      rho = red[0] / red[1];
+      // one thread divides: a warp's FP64 instruction holds its sub-partition's FP64 pipe
+      // for 64 cycles whether one lane or 32 are active, so 16 warps each dividing would
+      // cost as much as a pass over the grid
+      if (tid == 0) sh_rho[0] = red[0] / red[1];
+      __syncthreads();
+      rho = sh_rho[0];
     }
     {
       double v[2] = {0.0, 0.0};
@@ -491,14 +497,16 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
       r2 = red[0];
       m2 = red[1];
     }
-    // relative eigen-residual |r| / (rho |M x|) < tol
-    if (r2 < a.tol * a.tol * rho * rho * m2) break;
+    // relative eigen-residual |r| / (rho |M x|) < tol, decided by thread 0 and read after
+    // the barrier that follows the V-cycle's first loads
+    if (tid == 0) sh_stop = r2 < a.tol * a.tol * rho * rho * m2;
     // preconditioner: one V-cycle for K w = r from w = 0, all grids on chip
     for (int q = tid; q < nn; q += nt) {
       lv[0].f[q] = m0[q] ? (T)R[q] : (T)0;
       lv[0].x[q] = (T)0;
     }
     __syncthreads();
+    if (sh_stop) break;
     for (int d = 0; d + 1 < nlev; ++d) {
       tail_smooth<T, KK>(G, lv[d], a.pre, false, (T)a.omega);
       tail_restrict<T, KK>(G, lv[d], lv[d + 1], a.pre >= 1 && a.omega == 1.0);
@@ -581,7 +589,6 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
     __syncthreads();
     apply_km64();
   }
-  res = sqrt(r2) / (rho * sqrt(m2));
   double v[3] = {0.0, 0.0, 0.0};
   for (int q = tid; q < nn; q += nt) {
     v[0] += X[q] * KX[q];
@@ -589,8 +596,12 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
     v[2] += X[q];
   }
   block_sum_t<3>(v, stage, red);
-  const double lam = red[0] / red[1];
-  const double sc = (red[2] >= 0 ? 1.0 : -1.0) / sqrt(red[1]);
+  if (tid == 0) {
+    sh_rho[0] = red[0] / red[1];
+    sh_rho[1] = (red[2] >= 0 ? 1.0 : -1.0) / sqrt(red[1]);
+  }
+  __syncthreads();
+  const double lam = sh_rho[0], sc = sh_rho[1];
   double* out = a.ut1 + (long long)p * gl.bstride;
   const int gp = gl.pitch[1 - MLEV_LMIN];
   L1_FOR_NODES { out[(long long)j * gp + i] = sc * X[j * W + i]; }
@@ -598,6 +609,7 @@ __global__ void __launch_bounds__(512) k_level1_sm(DevGeom G, GlobalLayout gl, L
   const int ncoef = (G.ncx + 1) * (G.ncy + 1);
   for (int q = tid; q < ncoef; q += nt) a.c[(long long)p * ncoef + q] = 0.0;
   if (tid == 0) {
+    res = sqrt(r2) / (rho * sqrt(m2));
     a.c0[p] = 1.0;
     a.lam[p * a.lam_stride + 1] = lam;
     a.stat[p * a.stat_stride + MLEV_STAT_L1_IT] = it;
@@ -803,6 +815,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   extern __shared__ double rr_sm[];
   __shared__ double stage[4 * 256];  // FP64 block sums, one warp per quantity (block_sum_t)
   __shared__ double red[4];
+  __shared__ double sh_bc[2];  // scalars formed by thread 0 and broadcast at the next barrier
   __shared__ int bflag;
   const int p = blockIdx.x, N = a.nhb, bw = a.bw, bw1 = bw + 1;
   const int ncx = G.ncx, ncy = G.ncy;
@@ -832,30 +845,40 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
   float* xp = yp + vecs;
   float* bwork = xp + vecs;
   int* pairs = reinterpret_cast<int*>(a.smem ? bwork + (a.blocked ? 2 * TS : 0) : reinterpret_cast<float*>(rr_sm));
-  if (a.smem) {
-    for (int q = threadIdx.x; q < 32; q += blockDim.x) r32[N + q] = 0.f;
-    for (long long q = threadIdx.x; q < 2 * vecs; q += blockDim.x) yp[q] = 0.f;  // padding stays 0
+  // Set-up is a few rounds of L2 latency: the copies into shared memory (the factors of
+  // S(sigma) prepared ahead, K_H and M_H) are issued first as asynchronous copies, then the
+  // independent loads of the partials and the previous eigenvector, and one wait at the end.
+  const bool pre_in = a.use_pre && a.blocked && a.smem;
+  int pre_ok = 0;
+  double pre_sig = NAN;
+  if (pre_in) {
+    // factors of S(sigma) from the inner-product kernel (rr_prefactor_block), copied whether
+    // or not they are valid (invalid ones are rebuilt by factor() before any use)
+    const unsigned char* pp = a.pre + (long long)p * a.pre_stride;
+    const float* src = reinterpret_cast<const float*>(pp + 16);
+    for (long long q = threadIdx.x; q < 3 * tiles / 4; q += blockDim.x) cp_async16(Dinv + 4 * q, src + 4 * q);
+    pre_ok = *reinterpret_cast<const int*>(pp + 8);
+    pre_sig = *reinterpret_cast<const double*>(pp);
   }
   const double* KH = a.KH + (long long)p * N * bw1;
   const double* MH = a.MH + (long long)p * N * bw1;
   if (a.smem) {
     if (a.blocked && bw >= 3) {
       // only the nonzero diagonals d = 0, 1, b, b + 1 are read in blocked mode (products,
-      // S(mu), the block factor): stage those, independent loads several per thread
-#pragma unroll 4
+      // S(mu), the block factor): stage those
       for (int q = threadIdx.x; q < 4 * N; q += blockDim.x) {
         const long long e = (long long)(q >> 2) * bw1 + coarse_band_diag(q & 3, bw - 1);
-        kh_s[e] = KH[e];
-        mh_s[e] = MH[e];
+        cp_async8(kh_s + e, KH + e);
+        cp_async8(mh_s + e, MH + e);
       }
     } else {
       for (long long q = threadIdx.x; q < (long long)N * bw1; q += blockDim.x) {
-        kh_s[q] = KH[q];
-        mh_s[q] = MH[q];
+        cp_async8(kh_s + q, KH + q);
+        cp_async8(mh_s + q, MH + q);
       }
     }
-    KH = kh_s;
-    MH = mh_s;
+    for (int q = threadIdx.x; q < 32; q += blockDim.x) r32[N + q] = 0.f;
+    for (long long q = threadIdx.x; q < 2 * vecs; q += blockDim.x) yp[q] = 0.f;  // padding stays 0
   }
   double smu = NAN;  // mu of the S band in sm_s (shared-memory mode)
   // r_q = w_q - (S(mu) y)_q, from the staged S(mu) band when it is current (only the
@@ -884,6 +907,31 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     while ((aa + 1) * (aa + 2) / 2 <= q) ++aa;
     pairs[q] = (aa << 16) | (q - aa * (aa + 1) / 2);
   }
+  // g_a, g_b from the per-cell partials, and y from the previous level's eigenvector,
+  // y = -c_H / c_0, whose coarse part differs from this level's by the small change of
+  // u_{h_k} between levels (the previous solution warm-starts the first solve). c_prev and
+  // this level's output c may be the same buffer: it is read here, written at the end.
+  {
+    const int ncoef0 = (ncx + 1) * (ncy + 1);
+    const double* cpv = a.c_prev + (long long)p * ncoef0;
+    const double c0v = a.c0_prev[p];
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      const int X = q % (ncx - 1) + 1, Y = q / (ncx - 1) + 1;
+      double sa = 0.0, sb = 0.0, yq = 0.0;
+      if (is_free(G, 0, ncx, ncy, X, Y)) {
+        const double* c11 = part + ((Y - 1) * ncx + (X - 1)) * 12;
+        const double* c01 = part + ((Y - 1) * ncx + X) * 12;
+        const double* c10 = part + (Y * ncx + (X - 1)) * 12;
+        const double* c00 = part + (Y * ncx + X) * 12;
+        sa = c00[3] + c10[4] + c01[5] + c11[6];
+        sb = c00[7] + c10[8] + c01[9] + c11[10];
+        if (c0v != 0.0) yq = -cpv[Y * (ncx + 1) + X] / c0v;
+      }
+      ga[q] = sa;
+      gb[q] = sb;
+      y[q] = yq;
+    }
+  }
   {
     double v[3] = {0.0, 0.0, 0.0};
     for (int q = threadIdx.x; q < ncx * ncy; q += blockDim.x) {
@@ -894,21 +942,16 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     block_sum_t<3>(v, stage, red);
   }
   const double alpha = red[0], beta = red[1], sigma = red[2];
-  for (int q = threadIdx.x; q < N; q += blockDim.x) {
-    const int X = q % (ncx - 1) + 1, Y = q / (ncx - 1) + 1;
-    double sa = 0.0, sb = 0.0;
-    if (is_free(G, 0, ncx, ncy, X, Y)) {
-      const double* c11 = part + ((Y - 1) * ncx + (X - 1)) * 12;
-      const double* c01 = part + ((Y - 1) * ncx + X) * 12;
-      const double* c10 = part + (Y * ncx + (X - 1)) * 12;
-      const double* c00 = part + (Y * ncx + X) * 12;
-      sa = c00[3] + c10[4] + c01[5] + c11[6];
-      sb = c00[7] + c10[8] + c01[9] + c11[10];
-    }
-    ga[q] = sa;
-    gb[q] = sb;
-  }
+  // FP64 scalar work is formed by one thread: a warp's FP64 instruction holds its
+  // sub-partition's FP64 pipe for 64 cycles whether one lane or 32 are active, so every
+  // warp repeating a division costs the block as much as a vector operation
+  if (threadIdx.x == 0) sh_bc[0] = alpha / beta;
+  cp_async_wait_all();
   __syncthreads();
+  if (a.smem) {
+    KH = kh_s;
+    MH = mh_s;
+  }
   auto band_mv = [&](const double* M, const double* v, int q) { return coarse_band_mv(M, bw, bb, v, q, N); };
   double sig = NAN;  // shift of the current factors
   // FP32 factors of S(mu); false if S(mu) is not positive definite. Blocked mode: the block
@@ -932,19 +975,7 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     return true;
   };
   // w = w(mu) and r = w - S(mu) y for the current y (the previous solution warm-starts the
-  // next solve). y starts from the previous level's eigenvector, y = -c_H / c_0, whose
-  // coarse part differs from this level's by the small change of u_{h_k} between levels.
-  {
-    const int ncoef0 = (ncx + 1) * (ncy + 1);
-    const double* cpv = a.c_prev + (long long)p * ncoef0;
-    const double c0v = a.c0_prev[p];
-    // c_prev and this level's output c may be the same buffer: read all of it before any write
-    for (int q = threadIdx.x; q < N; q += blockDim.x) {
-      const int X = q % (ncx - 1) + 1, Y = q / (ncx - 1) + 1;
-      y[q] = (c0v != 0.0 && is_free(G, 0, ncx, ncy, X, Y)) ? -cpv[Y * (ncx + 1) + X] / c0v : 0.0;
-    }
-  }
-  __syncthreads();
+  // next solve)
   auto start = [&](double mu) {
     for (int q = threadIdx.x; q < N; q += blockDim.x) wv[q] = ga[q] - mu * gb[q];
     if (a.smem && smu != mu) stage_s(mu);
@@ -977,7 +1008,8 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
       v[1] += wv[q] * wv[q];
     }
     block_sum_t<2>(v, stage, red);
-    return red[1] > 0.0 ? red[0] / red[1] : 0.0;
+    // FP32 ratio: it is only compared against the targets and the previous ratio
+    return red[1] > 0.0 ? (double)((float)red[0] / (float)red[1]) : 0.0;
   };
   // refine to rel^2 <= target; false if the iteration stalls first (then refactor at mu)
   auto solve = [&](double mu, double target) {
@@ -1004,35 +1036,25 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     fp = -beta + 2.0 * red[2] - red[3];
   };
   // squared relative residuals: Newton steps need y to ~1e-6 (the variational f then has a
-  // relative error ~1e-12); the eigenvector to ~1e-11 (or until the residual stops falling):
-  // its error enters the next level's eigenvalue squared, and the returned u at 1e-11 is far
-  // inside the 1e-6 eigenvector bar of the mixed path
-  const double kNewtonTarget = 1e-12, kFinalTarget = 1e-22;
+  // relative error ~1e-12); the eigenvector to ~1e-9 (or until the residual stops falling):
+  // its error enters the next level's eigenvalue squared (1e-18), and the returned u at 1e-9
+  // is far inside the 1e-6 eigenvector bar of the mixed path
+  const double kNewtonTarget = 1e-12, kFinalTarget = 1e-18;
   // Newton stops when its step is below kStep relative: f is concave with its pole at the
   // smallest coarse eigenvalue, a distance d of about 1 % of mu away, so the error left after
   // the last step is about step^2 / d, under 1e-12 relative (the mixed path's bar is 1e-8)
   const double kStep = 1e-7;
-  double mu = alpha / beta, lo = 0.0, hi = INFINITY, lam = NAN;
+  double mu = sh_bc[0], lo = 0.0, hi = INFINITY, lam = NAN;
   int it = 0, status = 0;
   bool have = false, factored = false;
-  if (a.use_pre && a.blocked && a.smem) {
-    // factors of S(sigma) prepared by the inner-product kernel just before (rr_prefactor_block)
-    const unsigned char* pp = a.pre + (long long)p * a.pre_stride;
-    if (*reinterpret_cast<const int*>(pp + 8)) {
-      const float* src = reinterpret_cast<const float*>(pp + 16);
-      // float4 copies, several in flight per thread (L2 latency, not bandwidth, bounds this)
-      const float4* s4 = reinterpret_cast<const float4*>(src);
-      float4* d4 = reinterpret_cast<float4*>(Dinv);
-#pragma unroll 4
-      for (long long q = threadIdx.x; q < 3 * tiles / 4; q += blockDim.x) d4[q] = s4[q];
-      sig = *reinterpret_cast<const double*>(pp);
-      factored = true;
-    }
-    __syncthreads();
+  if (pre_in && pre_ok) {
+    // the factors of S(sigma) copied at set-up are valid
+    sig = pre_sig;
+    factored = true;
     // Newton from the extrapolated shift: it lies within ~1e-7 of lambda_L where alpha / beta
     // lies ~1e-4 above it, which saves a step (S(sigma) factored, so sigma is below the pole;
     // from either side of the root the safeguarded iteration converges)
-    if (factored && sig > 0.0 && sig < mu) mu = sig;
+    if (sig > 0.0 && sig < mu) mu = sig;
   }
   for (; it < a.max_iter; ++it) {
     bool ok = factored && solve(mu, kNewtonTarget);
@@ -1052,7 +1074,9 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     eval(mu, f, fp);
     if (f > 0.0) lo = mu;
     else hi = mu;
-    const double step = (fp < 0.0) ? -f / fp : 0.0;
+    // the step in FP32 division: its relative error 1e-7 only perturbs the next iterate, and
+    // the accepted last step is below kStep |mu|, so lambda gains an error under 1e-14
+    const double step = (fp < 0.0) ? (double)(-(float)f / (float)fp) : 0.0;
     if (fp < 0.0 && fabs(step) <= kStep * fabs(mu)) {
       lam = mu + step;
       break;
@@ -1088,14 +1112,17 @@ __global__ void __launch_bounds__(256) k_rr_mixed(DevGeom G, RRArgs a) {
     v[2] += y[q];
   }
   block_sum_t<3>(v, stage, red);
-  const double bn = red[0] - 2.0 * red[1] + beta;
-  const double S = (double)(1LL << (2 * a.L));
-  const double integral = sigma - S * red[2];
-  const double sc = (integral >= 0 ? 1.0 : -1.0) / sqrt(bn);
+  if (threadIdx.x == 0) {
+    const double bn = red[0] - 2.0 * red[1] + beta;
+    const double S = (double)(1LL << (2 * a.L));
+    const double integral = sigma - S * red[2];
+    sh_bc[1] = (integral >= 0 ? 1.0 : -1.0) / sqrt(bn);
+  }
   const int ncoef = (ncx + 1) * (ncy + 1);
   double* cp = a.c + (long long)p * ncoef;
   for (int q = threadIdx.x; q < ncoef; q += blockDim.x) cp[q] = 0.0;
   __syncthreads();
+  const double sc = sh_bc[1];
   for (int q = threadIdx.x; q < N; q += blockDim.x) {
     const int X = q % (ncx - 1) + 1, Y = q / (ncx - 1) + 1;
     cp[Y * (ncx + 1) + X] = is_free(G, 0, ncx, ncy, X, Y) ? -sc * y[q] : 0.0;
