@@ -268,12 +268,11 @@ __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pi
           const float pv = __shfl_sync(0xffffffffu, v[k], k);
           const float f = __shfl_sync(0xffffffffu, v[k], r);  // A(r, k) of the current step
           if (!(pv > 0.f)) ok = 0;
-          const float ip = __frcp_rn(pv);
+          // one update for every row: row r -= g (pivot row) with g = A(r, k) / p, and for the
+          // pivot row itself g = (p - 1) / p, which leaves it divided by p; one FMA per entry
+          const float g = (r == k ? f - 1.f : f) * __frcp_rn(pv);
 #pragma unroll
-          for (int c = 0; c < BS; ++c) {
-            const float pr = __shfl_sync(0xffffffffu, v[c], k + 16 * hi) * ip;
-            v[c] = (r == k) ? pr : v[c] - f * pr;
-          }
+          for (int c = 0; c < BS; ++c) v[c] = fmaf(-g, __shfl_sync(0xffffffffu, v[c], k + 16 * hi), v[c]);
         }
         if (hi)
 #pragma unroll

@@ -106,71 +106,103 @@ __device__ bool small_geneig(int n, const double A[3][3], const double B[3][3], 
   return true;
 }
 
-// Same computation in either precision (R = float or double); off_tol is the relative size
-// of the off-diagonal part at which the Jacobi sweeps stop.
-// Smallest eigenpair of the symmetric-definite pencil (A, B) of order n <= 3 with
+// Reciprocal and reciprocal square root: the fast rounded FP32 forms for float (these
+// pencils only weight search directions), the plain operations for double.
+__device__ __forceinline__ float sg_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double sg_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sg_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double sg_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+// Same computation in either precision (R = float or double) with the order N fixed at
+// compile time, so the 3 x 3 arrays live in registers; off_tol is the relative size of the
+// off-diagonal part at which the Jacobi sweeps stop.
+// Smallest eigenpair of the symmetric-definite pencil (A, B) of order N <= 3 with
 // symmetric diagonal scaling, Cholesky of B and cyclic Jacobi rotations. Returns false
 // if B is numerically singular.
-template <typename R>
-__device__ bool small_geneig_t(int n, const R A[3][3], const R B[3][3], R& theta, R coef[3], R off_tol) {
-  R d[3], As[3][3], Bs[3][3], Lc[3][3] = {{0}}, C[3][3], V[3][3];
-  for (int i = 0; i < n; ++i) d[i] = (R)1 / sqrt(B[i][i]);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
+template <typename R, int N>
+__device__ bool small_geneig_n(const R A[3][3], const R B[3][3], R& theta, R coef[3], R off_tol) {
+  R d[3], As[3][3], Bs[3][3], Lc[3][3] = {{0}}, iL[3], C[3][3], V[3][3];
+#pragma unroll
+  for (int i = 0; i < N; ++i) d[i] = sg_rsqrt(B[i][i]);
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
       As[i][j] = A[i][j] * d[i] * d[j];
       Bs[i][j] = B[i][j] * d[i] * d[j];
     }
-  for (int j = 0; j < n; ++j) {
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
     R s = Bs[j][j];
+#pragma unroll
     for (int k = 0; k < j; ++k) s -= Lc[j][k] * Lc[j][k];
     if (!(s > (R)1e-10)) return false;
     Lc[j][j] = sqrt(s);
-    for (int i = j + 1; i < n; ++i) {
+    iL[j] = sg_rcp(Lc[j][j]);
+#pragma unroll
+    for (int i = j + 1; i < N; ++i) {
       R t = Bs[i][j];
+#pragma unroll
       for (int k = 0; k < j; ++k) t -= Lc[i][k] * Lc[j][k];
-      Lc[i][j] = t / Lc[j][j];
+      Lc[i][j] = t * iL[j];
     }
   }
   // C = L^{-1} As L^{-T}: Y = L^{-1} As, then C = (L^{-1} Y^T)^T
   R Y[3][3];
-  for (int c = 0; c < n; ++c)
-    for (int i = 0; i < n; ++i) {
+#pragma unroll
+  for (int c = 0; c < N; ++c)
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
       R t = As[i][c];
+#pragma unroll
       for (int k = 0; k < i; ++k) t -= Lc[i][k] * Y[k][c];
-      Y[i][c] = t / Lc[i][i];
+      Y[i][c] = t * iL[i];
     }
-  for (int r = 0; r < n; ++r)
-    for (int i = 0; i < n; ++i) {
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
       R t = Y[r][i];
+#pragma unroll
       for (int k = 0; k < i; ++k) t -= Lc[i][k] * C[r][k];
-      C[r][i] = t / Lc[i][i];
+      C[r][i] = t * iL[i];
     }
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) V[i][j] = (R)(i == j);
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) V[i][j] = (R)(i == j);
   for (int sweep = 0; sweep < 30; ++sweep) {
     R off = 0.0;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) off += C[p][q] * C[p][q];
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+      for (int q = p + 1; q < N; ++q) off += C[p][q] * C[p][q];
     R dg = (R)0;
-    for (int p = 0; p < n; ++p) dg += C[p][p] * C[p][p];
+#pragma unroll
+    for (int p = 0; p < N; ++p) dg += C[p][p] * C[p][p];
     if (off <= off_tol * dg) break;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        if (C[p][q] == 0.0) continue;
-        const R tau = (C[q][q] - C[p][p]) / ((R)2 * C[p][q]);
-        const R t = (tau >= 0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
-        const R cs = (R)1 / sqrt((R)1 + t * t), sn = t * cs;
-        for (int k = 0; k < n; ++k) {
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+      for (int q = p + 1; q < N; ++q) {
+        if (C[p][q] == (R)0) continue;
+        const R tau = (C[q][q] - C[p][p]) * sg_rcp((R)2 * C[p][q]);
+        const R t = (tau >= 0 ? (R)1 : (R)-1) * sg_rcp(fabs(tau) + sqrt((R)1 + tau * tau));
+        const R cs = sg_rsqrt((R)1 + t * t), sn = t * cs;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
           const R a = C[k][p], b = C[k][q];
           C[k][p] = cs * a - sn * b;
           C[k][q] = sn * a + cs * b;
         }
-        for (int k = 0; k < n; ++k) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
           const R a = C[p][k], b = C[q][k];
           C[p][k] = cs * a - sn * b;
           C[q][k] = sn * a + cs * b;
         }
-        for (int k = 0; k < n; ++k) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
           const R a = V[k][p], b = V[k][q];
           V[k][p] = cs * a - sn * b;
           V[k][q] = sn * a + cs * b;
@@ -178,18 +210,35 @@ __device__ bool small_geneig_t(int n, const R A[3][3], const R B[3][3], R& theta
       }
   }
   int im = 0;
-  for (int i = 1; i < n; ++i)
-    if (C[i][i] < C[im][im]) im = i;
-  theta = C[im][im];
-  // coef = D L^{-T} v
-  R y[3];
-  for (int i = n - 1; i >= 0; --i) {
-    R t = V[i][im];
-    for (int k = i + 1; k < n; ++k) t -= Lc[k][i] * y[k];
-    y[i] = t / Lc[i][i];
+  R cm = C[0][0];
+#pragma unroll
+  for (int i = 1; i < N; ++i)
+    if (C[i][i] < cm) {
+      cm = C[i][i];
+      im = i;
+    }
+  theta = cm;
+  // coef = D L^{-T} v (the column of V chosen by select, no dynamic register indexing)
+  R vm[3];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    vm[i] = V[i][0];
+#pragma unroll
+    for (int c = 1; c < N; ++c)
+      if (im == c) vm[i] = V[i][c];
   }
-  for (int i = 0; i < n; ++i) coef[i] = d[i] * y[i];
-  for (int i = n; i < 3; ++i) coef[i] = (R)0;
+  R y[3];
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    R t = vm[i];
+#pragma unroll
+    for (int k = i + 1; k < N; ++k) t -= Lc[k][i] * y[k];
+    y[i] = t * iL[i];
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) coef[i] = d[i] * y[i];
+#pragma unroll
+  for (int i = N; i < 3; ++i) coef[i] = (R)0;
   return true;
 }
 
@@ -384,9 +433,11 @@ template void launch_level1<double>(const DevGeom&, const GlobalLayout&, const L
 // (A - rho B)_{xw} = r^T w and (A - rho B)_{xx} = 0, so FP32 resolves the small
 // coefficients of w and p; an FP32 coefficient error only makes a step slightly
 // suboptimal. Layout: FP32 Gram partials [11][threads], 4 FP64 vectors, 6 FP32 vectors,
-// then x (T) and f (T) of every level and the unknown masks.
-template <typename T, int KK>
-__global__ void __launch_bounds__(512, 1) k_level1_sm(DevGeom G, GlobalLayout gl, Level1Args a) {
+// then x (T) and f (T) of every level and the unknown masks. MINB is the register bound's
+// blocks per SM: 1 (126 registers, no spills) for one or few problems, 2 (64 registers)
+// when a batch has more problems than SMs and two blocks' shared memory fit one SM.
+template <typename T, int KK, int MINB>
+__global__ void __launch_bounds__(512, MINB) k_level1_sm(DevGeom G, GlobalLayout gl, Level1Args a) {
   extern __shared__ __align__(16) unsigned char l1_raw[];
   __shared__ SmGrid<T> lv[kTailMaxLev];
   __shared__ double red[4];
@@ -558,8 +609,8 @@ __global__ void __launch_bounds__(512, 1) k_level1_sm(DevGeom G, GlobalLayout gl
                               {gram[1], gram[4] - rf * gram[5], gram[6] - rf * gram[7]}};
       const float Bs[3][3] = {{gram[8], gram[9], gram[10]}, {gram[9], gram[3], gram[5]}, {gram[10], gram[5], gram[7]}};
       float th, cf[3];
-      bool ok = have_p && small_geneig_t<float>(3, As, Bs, th, cf, 1e-12f);
-      if (!ok) ok = small_geneig_t<float>(2, As, Bs, th, cf, 1e-12f);
+      bool ok = have_p && small_geneig_n<float, 3>(As, Bs, th, cf, 1e-12f);
+      if (!ok) ok = small_geneig_n<float, 2>(As, Bs, th, cf, 1e-12f);
       if (!ok) {
         cf[0] = 1.f;
         cf[1] = cf[2] = 0.f;
@@ -627,20 +678,32 @@ size_t level1_smem_bytes(long long nn0, long long tot, int tsize) {
 
 template <typename T>
 void launch_level1_sm(const DevGeom& G, const GlobalLayout& gl, const Level1Args& a, size_t smem, cudaStream_t s) {
+  // two blocks per SM pay only when the batch fills every SM once and still has problems left
+  int dev = 0, nsm = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const bool two = a.B > nsm && 2 * (smem + 4096) <= (size_t)smem_sm;
   switch (G.kap.kind) {
-#define L1_CASE(KKV)                                                                                     \
-  {                                                                                                      \
-    static bool attr = false;                                                                            \
-    if (!attr) {                                                                                         \
-      cudaFuncSetAttribute(k_level1_sm<T, KKV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kL1SmemMax); \
-      attr = true;                                                                                       \
-    }                                                                                                    \
-    k_level1_sm<T, KKV><<<a.B, dim3(32, 16), smem, s>>>(G, gl, a);                                       \
+#define L1_LAUNCH(KKV, MB)                                                                                   \
+  {                                                                                                          \
+    static bool attr = false;                                                                                \
+    if (!attr) {                                                                                             \
+      cudaFuncSetAttribute(k_level1_sm<T, KKV, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kL1SmemMax); \
+      attr = true;                                                                                           \
+    }                                                                                                        \
+    k_level1_sm<T, KKV, MB><<<a.B, dim3(32, 16), smem, s>>>(G, gl, a);                                       \
   }
+#define L1_CASE(KKV)        \
+  if (two)                  \
+    L1_LAUNCH(KKV, 2)       \
+  else                      \
+    L1_LAUNCH(KKV, 1)
     case MLEV_KAPPA_ONE: L1_CASE(MLEV_KAPPA_ONE) break;
     case MLEV_KAPPA_PER_COARSE_CELL: L1_CASE(MLEV_KAPPA_PER_COARSE_CELL) break;
     default: L1_CASE(MLEV_KAPPA_PER_FINE_ELEM) break;
 #undef L1_CASE
+#undef L1_LAUNCH
   }
 }
 template void launch_level1_sm<float>(const DevGeom&, const GlobalLayout&, const Level1Args&, size_t, cudaStream_t);

@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) k_mg_up(DevGeom G, const Tile* __restrict
 
 // tiles[b].grid = the job's grid at the first tail depth; its coarser grids follow it.
 template <typename T, int KK>
-__global__ void __launch_bounds__(512) k_mg_tail(DevGeom G, const Tile* __restrict__ tiles, T* X, T* F,
+__global__ void __launch_bounds__(512, KK == MLEV_KAPPA_PER_FINE_ELEM ? 2 : 3) k_mg_tail(DevGeom G, const Tile* __restrict__ tiles, T* X, T* F,
                                                  const T* __restrict__ inv, int nd_max, int nlev, int pre, int post,
                                                  int csweeps, T omega, int load_x) {
   extern __shared__ unsigned char sm_raw[];

@@ -19,24 +19,29 @@ struct SmGrid {
   const GridDesc* g;
 };
 
-// Red-black sweeps with a 32 x 16 thread block: thread (tx, ty) visits rows ty + 1, ty + 17,
-// ... and, in each row, the nodes of the current colour with stride 64.
+// Red-black sweeps, the nodes of one colour spread flat over the block: slot k is row
+// j = 1 + k / hw and the (k mod hw)-th node of the colour in that row (hw = nx / 2 slots per
+// row, the last one empty in rows with fewer), so every lane of every warp has a node and no
+// thread takes two while others idle. The nodes of a colour are independent, so the result
+// does not depend on the order.
 template <typename T, int KK>
 __device__ void tail_smooth(const DevGeom& G, const SmGrid<T>& s, int sweeps, bool reverse, T omega) {
   const GridDesc& g = *s.g;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int hw = s.nx >> 1, slots = hw * (s.ny - 1);
   for (int it = 0; it < sweeps; ++it)
     for (int cc = 0; cc < 2; ++cc) {
       const int color = reverse ? 1 - cc : cc;
-      for (int j = 1 + threadIdx.y; j < s.ny; j += blockDim.y) {
-        const int i0 = ((color + j) & 1) ? 1 : 2;
-        for (int i = i0 + 2 * threadIdx.x; i < s.nx; i += 2 * blockDim.x) {
-          const int q = j * s.W + i;
-          if (!s.m[q]) continue;
-          const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
-          const T v = s.f[q] + (T)w.e * s.x[q + 1] + (T)w.w * s.x[q - 1] + (T)w.n * s.x[q + s.W] +
-                      (T)w.s * s.x[q - s.W];
-          s.x[q] += omega * (div_diag<T>(v, (T)(w.e + w.w + w.n + w.s)) - s.x[q]);
-        }
+      for (int k = tid; k < slots; k += nt) {
+        const int r = k / hw, j = 1 + r;
+        const int i = (((color + j) & 1) ? 1 : 2) + 2 * (k - r * hw);
+        if (i >= s.nx) continue;
+        const int q = j * s.W + i;
+        if (!s.m[q]) continue;
+        const EW<T> w = edge_weights_t<T, KK>(G.kap, g.problem, g.level, g.ox + i, g.oy + j);
+        const T v = s.f[q] + (T)w.e * s.x[q + 1] + (T)w.w * s.x[q - 1] + (T)w.n * s.x[q + s.W] +
+                    (T)w.s * s.x[q - s.W];
+        s.x[q] += omega * (div_diag<T>(v, (T)(w.e + w.w + w.n + w.s)) - s.x[q]);
       }
       __syncthreads();
     }
@@ -53,39 +58,46 @@ __device__ __forceinline__ T tail_res(const DevGeom& G, const SmGrid<T>& s, int 
 }
 
 // f_c = P^T (f - A x)_fine, x_c = 0; black_zero as in k_restrict (pre-smoothed by plain
-// Gauss-Seidel ending black: only the red nodes of the coarse hat have a residual).
+// Gauss-Seidel ending black: only the red nodes of the coarse hat have a residual). Coarse
+// nodes flat over the block.
 template <typename T, int KK>
 __device__ void tail_restrict(const DevGeom& G, const SmGrid<T>& fi, const SmGrid<T>& co, bool black_zero) {
-  for (int J = threadIdx.y; J <= co.ny; J += blockDim.y)
-    for (int I = threadIdx.x; I <= co.nx; I += blockDim.x) {
-      const int q = J * co.W + I;
-      co.x[q] = (T)0;
-      if (!co.m[q]) continue;
-      const int i = 2 * I, j = 2 * J;
-      T half = tail_res<T, KK>(G, fi, i + 1, j + 1) + tail_res<T, KK>(G, fi, i - 1, j - 1);
-      if (!black_zero)
-        half += tail_res<T, KK>(G, fi, i + 1, j) + tail_res<T, KK>(G, fi, i - 1, j) +
-                tail_res<T, KK>(G, fi, i, j + 1) + tail_res<T, KK>(G, fi, i, j - 1);
-      co.f[q] = tail_res<T, KK>(G, fi, i, j) + (T)0.5 * half;
-    }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int nc = co.W * (co.ny + 1);
+  for (int q = tid; q < nc; q += nt) {
+    co.x[q] = (T)0;
+    if (!co.m[q]) continue;
+    const int J = q / co.W, I = q - J * co.W;
+    const int i = 2 * I, j = 2 * J;
+    T half = tail_res<T, KK>(G, fi, i + 1, j + 1) + tail_res<T, KK>(G, fi, i - 1, j - 1);
+    if (!black_zero)
+      half += tail_res<T, KK>(G, fi, i + 1, j) + tail_res<T, KK>(G, fi, i - 1, j) +
+              tail_res<T, KK>(G, fi, i, j + 1) + tail_res<T, KK>(G, fi, i, j - 1);
+    co.f[q] = tail_res<T, KK>(G, fi, i, j) + (T)0.5 * half;
+  }
   __syncthreads();
 }
 
-// x += P x_c; red_only as in k_prolong (the next half-sweep is black with omega = 1).
+// x += P x_c; red_only as in k_prolong (the next half-sweep is black with omega = 1): then
+// only the red nodes, in the flat colour slots of tail_smooth, else every interior node.
 template <typename T>
 __device__ void tail_prolong(const SmGrid<T>& fi, const SmGrid<T>& co, bool red_only) {
-  for (int j = 1 + threadIdx.y; j < fi.ny; j += blockDim.y)
-    for (int i = 1 + threadIdx.x; i < fi.nx; i += blockDim.x) {
-      const int q = j * fi.W + i;
-      if (!fi.m[q] || (red_only && ((i + j) & 1))) continue;
-      const int I = i >> 1, J = j >> 1, c = J * co.W + I;
-      T v;
-      if (!(i & 1) && !(j & 1)) v = co.x[c];
-      else if ((i & 1) && !(j & 1)) v = (T)0.5 * (co.x[c] + co.x[c + 1]);
-      else if (!(i & 1) && (j & 1)) v = (T)0.5 * (co.x[c] + co.x[c + co.W]);
-      else v = (T)0.5 * (co.x[c] + co.x[c + co.W + 1]);
-      fi.x[q] += v;
-    }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int hw = red_only ? fi.nx >> 1 : fi.nx - 1, slots = hw * (fi.ny - 1);
+  for (int k = tid; k < slots; k += nt) {
+    const int r = k / hw, j = 1 + r;
+    const int i = red_only ? ((j & 1) ? 1 : 2) + 2 * (k - r * hw) : 1 + (k - r * hw);
+    if (i >= fi.nx) continue;
+    const int q = j * fi.W + i;
+    if (!fi.m[q]) continue;
+    const int I = i >> 1, J = j >> 1, c = J * co.W + I;
+    T v;
+    if (!(i & 1) && !(j & 1)) v = co.x[c];
+    else if ((i & 1) && !(j & 1)) v = (T)0.5 * (co.x[c] + co.x[c + 1]);
+    else if (!(i & 1) && (j & 1)) v = (T)0.5 * (co.x[c] + co.x[c + co.W]);
+    else v = (T)0.5 * (co.x[c] + co.x[c + co.W + 1]);
+    fi.x[q] += v;
+  }
   __syncthreads();
 }
 
