@@ -269,8 +269,10 @@ __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pi
           const float f = __shfl_sync(0xffffffffu, v[k], r);  // A(r, k) of the current step
           if (!(pv > 0.f)) ok = 0;
           // one update for every row: row r -= g (pivot row) with g = A(r, k) / p, and for the
-          // pivot row itself g = (p - 1) / p, which leaves it divided by p; one FMA per entry
-          const float g = (r == k ? f - 1.f : f) * __frcp_rn(pv);
+          // pivot row itself g = (p - 1) / p, which leaves it divided by p; one FMA per entry.
+          // The approximate reciprocal (a few ulp) suffices for a preconditioner's factors and
+          // takes the rounding fix-up off the step's dependency chain.
+          const float g = (r == k ? f - 1.f : f) * __fdividef(1.0f, pv);
 #pragma unroll
           for (int c = 0; c < BS; ++c) v[c] = fmaf(-g, __shfl_sync(0xffffffffu, v[c], k + 16 * hi), v[c]);
         }
@@ -290,7 +292,7 @@ __device__ bool block_ldlt_f(const double* Sb, int bw1, int b, int nb, float* Pi
         for (int k = 0; k < BS; ++k) {
           const float pv = __shfl_sync(0xffffffffu, row[k], k);
           if (!(pv > 0.f)) ok = 0;
-          const float ip = __frcp_rn(pv);
+          const float ip = __fdividef(1.0f, pv);
           const float f = row[k];
 #pragma unroll
           for (int c = 0; c < BS; ++c) {
