@@ -21,7 +21,11 @@ eigenvalue problem") computes:
 * ``multiple``  - the same for the q smallest eigenpairs (the subspace form: one
                   correction per eigenpair, one Rayleigh-Ritz on
                   V_{0H} + span{u~_1 .. u~_q}; Section 4's multiple-eigenvalue remark,
-                  Table 1).
+                  Table 1);
+* ``tensor``    - Example 2's full-tensor coefficient and weighted mass (Section 6);
+* ``p2``        - quadratic elements for Example 1 (Section 6);
+* ``cube3d``    - the d = 3 case on box domains with Kuhn tetrahedra (Sections 2.1 and
+                  4.2), run through the same ``multilevel`` / ``multiple`` steps.
 
 Everything is float64, with sparse direct solves (``scipy.sparse.linalg.splu``)
 and dense generalized symmetric eigensolves (``scipy.linalg.eigh``).

@@ -248,3 +248,31 @@ def example2(levels: int = 4, parts: int = 4) -> Problem:
         levels=levels,
         notes={"forms": "example2"},
     )
+
+
+# --- d = 3 (Section 2.1 admits tetrahedra; the paper runs only d = 2) -----------------------
+
+@dataclass
+class Box3:
+    """A box (0, ncx H) x (0, ncy H) x (0, ncz H) of coarse cubes of side H, split into
+    parts^3 equal blocks D_j (a coarse-cube box each) with overlap o coarse cubes and inset
+    delta; n levels h_k = H / 2^k. Only the oracle takes it (no GPU path for d = 3)."""
+    name: str
+    nc: tuple
+    H: float
+    levels: int
+    parts: int
+    overlap: int
+    delta: float
+
+    def with_levels(self, n: int) -> "Box3":
+        return replace(self, levels=n, name=f"{self.name.rsplit('-n', 1)[0]}-n{n}")
+
+
+def unit_cube(nc: int, parts: int, levels: int, overlap: int = 1, delta_in_H: float = 0.5) -> Box3:
+    """The unit cube in nc^3 coarse cubes, parts^3 subdomain blocks (nc divisible by parts)."""
+    if nc % parts:
+        raise ValueError("nc must be a multiple of parts")
+    H = 1.0 / nc
+    return Box3(name=f"cube{nc}-m{parts ** 3}-o{overlap}-n{levels}", nc=(nc, nc, nc), H=H, levels=levels,
+                parts=parts, overlap=overlap, delta=delta_in_H * H)
